@@ -1,0 +1,166 @@
+"""Seeded synthetic snake workloads shared by the CUDA path's tests/bench and the oracle.
+
+This module only draws parameters.  It holds none of the simulation's arithmetic
+(no constraint, filter or integrator maths), so the oracle and the CUDA path can both
+consume its arrays without sharing any method code.
+
+A workload is a dict of numpy arrays, one entry per snake:
+
+  ints    : n_links, seg_per_link, n_fixed
+  floats  : L0, mass, alpha_s, alpha_b, gain, tau_inf, tau_def, mu, damping, radius,
+            gait_amp, gait_freq, gait_lag, gait_offset, gait_scale, gait_alternate,
+            x0, y0, z0, yaw0
+
+and a dict of global solver settings (dt, n_sub, iters, tol, omega, gravity, contact).
+
+The shapes follow the paper's snake (four soft links joined by rigid connectors, Sec. III
+and Sec. V) and its open-loop gait (Eq. 9, Sec. V-A): links are discretised into
+segments of equal rest length, pressure is normalised to [0, 1] per chamber, and the
+gait drives one chamber of each link at a time.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+INT_FIELDS = ("n_links", "seg_per_link", "n_fixed")
+FLOAT_FIELDS = (
+    "L0", "mass", "alpha_s", "alpha_b", "gain", "tau_inf", "tau_def", "mu",
+    "damping", "radius", "gait_amp", "gait_freq", "gait_lag", "gait_offset",
+    "gait_scale", "gait_alternate", "x0", "y0", "z0", "yaw0",
+)
+
+# Physical defaults of the 1D-actuator snake (segment length, node mass, compliances,
+# curvature gain, latency constants, friction, contact radius).
+DEFAULTS = dict(
+    L0=0.02, mass=0.01, alpha_s=1e-8, alpha_b=1e-4, gain=20.0, tau_inf=0.15,
+    tau_def=0.25, mu=0.5, damping=0.05, radius=0.01, gait_amp=1.0, gait_freq=1.0,
+    gait_lag=math.pi / 2, gait_offset=0.0, gait_scale=1.0, gait_alternate=0.0,
+    x0=0.0, y0=0.0, z0=0.01, yaw0=0.0,
+)
+
+
+def solver_settings(dt=1.0 / 60.0, n_sub=20, iters=10, tol=0.0, omega=1.0 / 3.0,
+                    gravity=(0.0, 0.0, -9.81), contact=True, warm=0):
+    """Global settings: env-step dt, substeps, iteration cap, residual tolerance
+    (0 = run exactly `iters` updates), Jacobi relaxation, gravity, ground contact on/off,
+    warm start (0 = cold, 1 = previous substep's multipliers, 2 = learned)."""
+    return dict(dt=float(dt), n_sub=int(n_sub), iters=int(iters), tol=float(tol),
+                omega=float(omega), gravity=tuple(float(g) for g in gravity),
+                contact=bool(contact), warm=int(warm))
+
+
+def _base(n: int) -> dict:
+    w = {k: np.full(n, DEFAULTS[k], dtype=np.float64) for k in FLOAT_FIELDS}
+    w["n_links"] = np.full(n, 4, dtype=np.int32)
+    w["seg_per_link"] = np.full(n, 10, dtype=np.int32)
+    w["n_fixed"] = np.zeros(n, dtype=np.int32)
+    return w
+
+
+def n_nodes(w: dict) -> np.ndarray:
+    return (w["n_links"].astype(np.int64) * w["seg_per_link"] + 1)
+
+
+def subset(w: dict, idx) -> dict:
+    idx = np.asarray(idx)
+    return {k: np.ascontiguousarray(v[idx]) for k, v in w.items()}
+
+
+def single_snake() -> dict:
+    """One 4-link snake (41 nodes).  Link i is driven with 0.5 + 0.5 sin(2 pi t + i pi/2)
+    on alternating sides (sign (-1)^i), mu = 0.5."""
+    w = _base(1)
+    w["gait_offset"][:] = 0.5
+    w["gait_scale"][:] = 0.5
+    w["gait_amp"][:] = 1.0
+    w["gait_freq"][:] = 1.0
+    w["gait_lag"][:] = math.pi / 2
+    w["gait_alternate"][:] = 1.0
+    w["mu"][:] = 0.5
+    return w
+
+
+def static_sweep(seed: int = 2, n_press: int = 16, n_comp: int = 16) -> dict:
+    """Cantilevered single actuators (10 segments, nodes 0 and 1 clamped) held in the air,
+    constant chamber pressure on 16 uniformly spaced levels in [0, 1] crossed with 16
+    bend compliances drawn log-uniform in [1e-5, 1e-3]."""
+    rng = np.random.default_rng(seed)
+    n = n_press * n_comp
+    w = _base(n)
+    press = np.linspace(0.0, 1.0, n_press)
+    comp = 10.0 ** rng.uniform(-5.0, -3.0, size=n_comp)
+    P, C = np.meshgrid(press, comp, indexing="ij")
+    w["n_links"][:] = 1
+    w["n_fixed"][:] = 2
+    w["alpha_b"][:] = C.ravel()
+    # constant command u = p on the "right" chamber: offset p, no oscillation
+    w["gait_offset"][:] = P.ravel()
+    w["gait_scale"][:] = 0.0
+    w["gait_amp"][:] = 1.0
+    w["gait_freq"][:] = 0.0
+    w["z0"][:] = 1.0
+    return w
+
+
+def batched(n: int = 4096, seed: int = 3, links=(2, 8)) -> dict:
+    """Uneven batch: link counts uniform in {2..8}, gait amplitude U[0.3, 1], frequency
+    U[0.5, 2] Hz, phase lag U[pi/4, pi], mu U[0.3, 0.8], initial yaw U[0, 2 pi),
+    zero offset (the paper's gait, Eq. 9, with phi = 0)."""
+    rng = np.random.default_rng(seed)
+    w = _base(n)
+    w["n_links"][:] = rng.integers(links[0], links[1] + 1, size=n)
+    w["gait_amp"][:] = rng.uniform(0.3, 1.0, size=n)
+    w["gait_freq"][:] = rng.uniform(0.5, 2.0, size=n)
+    w["gait_lag"][:] = rng.uniform(math.pi / 4, math.pi, size=n)
+    w["mu"][:] = rng.uniform(0.3, 0.8, size=n)
+    w["yaw0"][:] = rng.uniform(0.0, 2 * math.pi, size=n)
+    w["gait_offset"][:] = 0.0
+    w["gait_scale"][:] = 1.0
+    return w
+
+
+def learned(n: int = 16384, seed: int = 4) -> dict:
+    """Evaluation batch for the learned warm start (drawn like `batched`)."""
+    return batched(n=n, seed=seed)
+
+
+def training_seeds(k: int = 4, base: int = 1000) -> list[int]:
+    """Seeds for the logged training data; disjoint from every evaluation seed (< 1000)."""
+    return [base + i for i in range(k)]
+
+
+def calibration(n: int = 1024, seed: int = 5) -> tuple[dict, dict]:
+    """Calibration batch: 4-link snakes.  Returns (ground truth, initial guess); both draw
+    bend compliance log-U[1e-5, 1e-3], damping U[0.01, 0.2], tau_inflate / tau_deflate
+    U[0.05, 0.4] s and curvature gain U[10, 30] rad/m; the gait is the paper's Eq. 9."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(2):
+        w = _base(n)
+        w["alpha_b"][:] = 10.0 ** rng.uniform(-5.0, -3.0, size=n)
+        w["damping"][:] = rng.uniform(0.01, 0.2, size=n)
+        w["tau_inf"][:] = rng.uniform(0.05, 0.4, size=n)
+        w["tau_def"][:] = rng.uniform(0.05, 0.4, size=n)
+        w["gain"][:] = rng.uniform(10.0, 30.0, size=n)
+        out.append(w)
+    shared = rng.uniform(size=(n, 3))
+    for w in out:
+        w["gait_amp"][:] = 0.5 + 0.5 * shared[:, 0]
+        w["gait_freq"][:] = 0.5 + 1.5 * shared[:, 1]
+        w["gait_lag"][:] = math.pi / 4 + (3 * math.pi / 4) * shared[:, 2]
+    return out[0], out[1]
+
+
+def pendulum(length: float = 0.1) -> dict:
+    """Two nodes: node 0 clamped, node 1 hanging at `length` (one stretch row)."""
+    w = _base(1)
+    w["n_links"][:] = 1
+    w["seg_per_link"][:] = 1
+    w["n_fixed"][:] = 1
+    w["L0"][:] = length
+    w["z0"][:] = 1.0
+    w["damping"][:] = 0.0
+    w["gait_amp"][:] = 0.0
+    return w
