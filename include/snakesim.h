@@ -1,0 +1,190 @@
+/*
+ * snakesim.h -- C-ABI of the GB300 soft-snake simulator.
+ *
+ * The library advances batches of soft robotic snakes built from 1D pneumatic
+ * actuators (Gasoto et al., "A Validated Physical Model For Real-Time Simulation of
+ * Soft Robotic Snakes", arXiv 1904.02833).  Each snake is a chain of particles
+ * (Sec. IV-A, Eq. 1: q_i = [x y z], lumped mass M_i = m 1_3) held together by compliant
+ * constraints c(q, p) + E lambda = 0 (Sec. IV, equations of motion).  Per env-step of
+ * length dt the library runs n_sub substeps of first-order implicit time stepping
+ * (Sec. IV-D); each substep
+ *   a1  samples the open-loop gait a_k = clamp(sin(w t + alpha k) + phi, -1, 1) A (Eq. 9),
+ *   a2  filters the two antagonistic chamber pressures of every link (Sec. III) through a
+ *       first-order inflate / deflate latency,
+ *   a3  turns pressure into rest curvature (Eq. 3-4: a chamber's rest length scales with
+ *       eps(p) = 1 + p / Y; with an inextensible centre layer this is a rest angle
+ *       G (p_R - p_L) L0 per node),
+ *   a4  predicts positions under gravity,
+ *   a5  relaxes the Schur system of Eq. 8 with its own diagonal (the Jacobi
+ *       preconditioner of Sec. IV-D) over stretch, yaw/pitch bend, ground contact
+ *       (Eq. 7) and Coulomb friction rows, in parallel, with compliance alpha / h^2,
+ *   a6  measures the normalised residual and stops at the tolerance or the cap,
+ *   a7  updates velocities from the displacement with exponential damping.
+ * Thousands of snakes of uneven length run in one persistent kernel.
+ *
+ * Conventions (every call):
+ *   - Every call returns a SimStatus; nothing aborts or throws across the ABI.  The text
+ *     of the last error of the calling thread is available from sim_last_error().
+ *   - Work is enqueued on the CUDA stream given to sim_create (a cudaStream_t passed as
+ *     void*, 0 = legacy default stream) and is asynchronous unless stated otherwise.
+ *   - The library owns its device buffers (allocated in sim_create, freed in
+ *     sim_destroy).  Caller buffers are only read or written during the call, or by work
+ *     enqueued by it on the handle's stream.
+ *   - Buffers flagged is_device = 1 are device pointers (e.g. from torch tensors);
+ *     is_device = 0 means host memory (copies are synchronous with the stream).
+ *   - Node arrays hold the snakes back to back: snake s owns nodes
+ *     [node_off[s], node_off[s+1]) with node_off[s+1] - node_off[s] = n_links * seg + 1,
+ *     and links [link_off[s], link_off[s+1]).
+ *   - A handle is used by one host thread at a time.
+ */
+#ifndef SNAKESIM_H_
+#define SNAKESIM_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct SimHandle SimHandle; /* opaque, owned by the library */
+
+typedef enum {
+  SIM_OK = 0,
+  SIM_NOT_CONVERGED = 1, /* warning: some snake hit the iteration cap above tol */
+  SIM_EINVAL = -1,       /* bad argument; nothing was enqueued */
+  SIM_ECUDA = -2,        /* a CUDA call failed; see sim_last_error() */
+  SIM_ENOMEM = -3,       /* device allocation failed */
+  SIM_ENAN = -4          /* a snake's state became non-finite */
+} SimStatus;
+
+/* Warm-start modes of the multipliers at the start of every substep. */
+enum { SIM_WARM_COLD = 0, SIM_WARM_PREVIOUS = 1, SIM_WARM_LEARNED = 2 };
+
+/* Global solver settings. */
+typedef struct {
+  double dt;          /* env-step length [s] (1/60 in the paper's real-time setting)     */
+  int32_t n_sub;      /* substeps per env-step, h = dt / n_sub                           */
+  int32_t iters;      /* cap on Jacobi updates per substep                               */
+  float tol;          /* residual tolerance; 0 runs exactly `iters` updates              */
+  float omega;        /* Jacobi relaxation (1/3: a node touches at most 3 bend rows)     */
+  float gravity[3];   /* [m/s^2]                                                         */
+  int32_t contact;    /* 1: ground plane z = 0 with Coulomb friction                     */
+  int32_t warm;       /* SIM_WARM_*                                                      */
+  int32_t reserved;
+} SimConfig;
+
+/* Per-snake parameters (host layout, 96 bytes). */
+typedef struct {
+  int32_t n_links;      /* soft links; nodes = n_links * seg_per_link + 1               */
+  int32_t seg_per_link; /* segments per link (rigid connector at every link boundary)   */
+  int32_t n_fixed;      /* leading nodes clamped in place (cantilever: 2)               */
+  int32_t reserved;
+  float L0;             /* segment rest length [m]                                       */
+  float mass;           /* node mass [kg]                                                */
+  float alpha_s;        /* stretch compliance [m/N]                                      */
+  float alpha_b;        /* bend compliance [m/N]; bend rows are L0 x angle               */
+  float gain;           /* rest curvature per unit pressure G [rad/m]                    */
+  float tau_inf;        /* inflation time constant [s]                                   */
+  float tau_def;        /* deflation time constant [s]                                   */
+  float mu;             /* Coulomb friction coefficient                                  */
+  float damping;        /* velocity damping rate d [1/s]: v <- v exp(-d h)               */
+  float radius;         /* contact radius r: contact row z - r >= 0 [m]                  */
+  float gait_amp;       /* A of Eq. 9 (pressure normalised to [0, 1])                    */
+  float gait_freq;      /* f [Hz], the sine is sin(2 pi f t + k lag)                     */
+  float gait_lag;       /* phase shift between links alpha [rad]                         */
+  float gait_offset;    /* phi of Eq. 9                                                  */
+  float gait_scale;     /* sine scale (1 in Eq. 9; 0 gives a constant command)           */
+  float gait_alternate; /* 1: sign (-1)^k on link k (pressure on alternating sides)      */
+  float x0, y0, z0;     /* position of node 0 [m]                                        */
+  float yaw0;           /* initial heading [rad]                                         */
+} SnakeParams;
+
+/* Creates a simulator for n_snakes snakes (params: host array of n_snakes) in the
+ * straight initial pose (node i at (x0, y0, z0) + i L0 (cos yaw0, sin yaw0, 0)), at
+ * rest, chambers empty, multipliers zero, time 0.  `stream` is a cudaStream_t (void*).
+ * Errors: SIM_EINVAL (null pointers, n_snakes < 1, n_links < 1, seg_per_link < 1,
+ * n_fixed outside [0, nodes], non-positive L0 / mass / dt / n_sub, iters < 0),
+ * SIM_ENOMEM, SIM_ECUDA.  On error *out is NULL. */
+SimStatus sim_create(const SimConfig* cfg, int n_snakes, const SnakeParams* params,
+                     void* stream, SimHandle** out);
+
+/* Replaces the solver settings (dt, n_sub, iters, tol, omega, gravity, contact, warm)
+ * for subsequent steps.  Same validation as sim_create. */
+SimStatus sim_set_config(SimHandle* h, const SimConfig* cfg);
+
+/* Overrides the gait: u[total_links] in [-1, 1] is the command of every link for every
+ * substep of subsequent sim_step calls (u > 0 drives the right chamber, u < 0 the
+ * left, Sec. III); u = NULL returns to the gait of Eq. 9.  The values are copied
+ * (stream-ordered) into a library buffer; the caller may reuse u after the call.
+ * Errors: SIM_EINVAL for a null handle. */
+SimStatus sim_set_pressure(SimHandle* h, const float* u, int is_device);
+
+/* Advances every snake by n_steps env-steps (asynchronous).  n_steps >= 0.
+ * The per-snake residual (max over the steps' substeps of the residual after the last
+ * update) and update counts (sum over substeps of the last env-step) are kept for
+ * sim_get_state.  Errors: SIM_EINVAL, SIM_ECUDA. */
+SimStatus sim_step(SimHandle* h, int n_steps);
+
+/* Reads the state.  Any pointer may be NULL.  pos, vel: [total_nodes][3] float;
+ * press: [total_links][2] (p_R, p_L); resid: [n_snakes] float; iters: [n_snakes] int32.
+ * is_device = 0 copies to host memory and synchronises the stream; is_device = 1
+ * enqueues device-to-device copies. */
+SimStatus sim_get_state(SimHandle* h, float* pos, float* vel, float* press, float* resid,
+                        int32_t* iters, int is_device);
+
+/* Overwrites the state (any pointer may be NULL: that part is kept).  Layouts as in
+ * sim_get_state; lam: [total_nodes][6] multipliers (stretch, yaw, pitch, contact,
+ * friction x, friction y of the rows a node owns). */
+SimStatus sim_set_state(SimHandle* h, const float* pos, const float* vel, const float* press,
+                        const float* lam, int is_device);
+
+/* Reads the multipliers [total_nodes][6] (layout as in sim_set_state). */
+SimStatus sim_get_lambda(SimHandle* h, float* lam, int is_device);
+
+/* Sizes: total nodes, total links, snakes; and the env-step counter (time = step * dt). */
+SimStatus sim_get_info(SimHandle* h, int64_t* n_nodes, int64_t* n_links, int32_t* n_snakes,
+                       int64_t* step_index);
+
+/* Sets the env-step counter (the gait time is step_index * dt). */
+SimStatus sim_set_step_index(SimHandle* h, int64_t step_index);
+
+/* Device pointers of the library-owned state, for zero-copy use from torch:
+ * pos4/vel4 [total_nodes] float4 (x, y, z, inverse mass) / (vx, vy, vz, 0),
+ * press2 [total_links] float2, lam [total_nodes][6] float.  Valid until sim_destroy. */
+SimStatus sim_device_state(SimHandle* h, void** pos4, void** vel4, void** press2, void** lam);
+
+/* Per-snake status of the last step: 0 ok, SIM_NOT_CONVERGED, SIM_ENAN (host array
+ * [n_snakes], synchronises the stream).  Returns the worst status. */
+SimStatus sim_get_status(SimHandle* h, int32_t* status);
+
+/* Chooses the lanes per snake and nodes per lane of every snake-length bucket by
+ * timing candidate layouts with CUDA events (the state is restored afterwards).
+ * Runs synchronously.  Errors: SIM_EINVAL, SIM_ECUDA. */
+SimStatus sim_autotune(SimHandle* h, int n_steps);
+
+/* Current layout of a bucket of snakes with `nodes` nodes: lanes per snake (8, 16, 32)
+ * and nodes per lane (1..4); 0 if no snake has that length. */
+SimStatus sim_get_layout(SimHandle* h, int nodes, int32_t* lanes, int32_t* nodes_per_lane);
+
+/* Forces the layout of a bucket (lanes in {8, 16, 32}, nodes_per_lane in 1..4,
+ * lanes * nodes_per_lane >= nodes).  Errors: SIM_EINVAL. */
+SimStatus sim_set_layout(SimHandle* h, int nodes, int lanes, int nodes_per_lane);
+
+/* Captures sim_step(h, n_steps) in a CUDA graph on first use and replays it
+ * afterwards (the graph is rebuilt when the configuration or layout changes). */
+SimStatus sim_step_graph(SimHandle* h, int n_steps);
+
+/* Kernel launches made by this handle so far (the count the benchmark reports). */
+SimStatus sim_launch_count(SimHandle* h, int64_t* launches);
+
+/* Frees the handle and its device buffers (synchronises the stream).  NULL is ok. */
+SimStatus sim_destroy(SimHandle* h);
+
+/* Text of the last error raised on the calling thread ("" if none). */
+const char* sim_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SNAKESIM_H_ */

@@ -1,0 +1,623 @@
+// Host runtime and C-ABI of the soft-snake simulator (see include/snakesim.h).
+//
+// Owns the structure-of-arrays state in HBM (float4 positions with inverse mass,
+// float4 velocities, float2 chamber pressures, six multipliers per node), buckets the
+// snakes by node count, picks a lane layout per bucket (lanes per snake x nodes per
+// lane, optionally by timing them: sim_autotune) and launches the persistent solver
+// kernel, directly or through a captured CUDA graph.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+#include "snakesim.h"
+#include "solver.cuh"
+
+using namespace snakesim;
+
+namespace {
+
+thread_local std::string g_err;
+
+SimStatus fail(SimStatus s, const std::string& msg) {
+  g_err = msg;
+  return s;
+}
+
+#define CU(call)                                                                       \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess)                                                             \
+      return fail(e_ == cudaErrorMemoryAllocation ? SIM_ENOMEM : SIM_ECUDA,            \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                 \
+  } while (0)
+
+}  // namespace
+
+// ------------------------------------------------------------------ kernels
+// One kernel per nodes-per-lane count (each gets the register budget of its own layout);
+// the host launches the ones that have work on forked streams so that they run together.
+template <int NPL>
+__global__ void __launch_bounds__(128) snake_solver_kernel(SolverArgs A) {
+  const int warp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  for (int it = warp; it < A.n_items; it += nwarps) {
+    const int4 item = A.items[it];
+    const int G = layout_lanes(item.z);
+    const int gi = lane / G;
+    const bool ok = gi < item.y;
+    const int snake = ok ? A.order[item.x + gi] : 0;
+    if (G == 8) run_group<NPL, 8>(A, snake, ok);
+    else if (G == 16) run_group<NPL, 16>(A, snake, ok);
+    else run_group<NPL, 32>(A, snake, ok);
+  }
+}
+
+typedef void (*SolverKernel)(SolverArgs);
+const SolverKernel kSolverKernels[4] = {snake_solver_kernel<1>, snake_solver_kernel<2>,
+                                        snake_solver_kernel<3>, snake_solver_kernel<4>};
+
+__global__ void pack_xyz_kernel(const float4* __restrict__ in, float* __restrict__ out, long long n) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < n) { float4 p = in[i]; out[3 * i] = p.x; out[3 * i + 1] = p.y; out[3 * i + 2] = p.z; }
+}
+
+__global__ void unpack_xyz_kernel(const float* __restrict__ in, float4* __restrict__ out, long long n,
+                                  const float* __restrict__ inv_mass) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < n) {
+    out[i] = make_float4(in[3 * i], in[3 * i + 1], in[3 * i + 2], inv_mass ? inv_mass[i] : 0.f);
+  }
+}
+
+// ------------------------------------------------------------------ handle
+struct SimHandle {
+  SimConfig cfg;
+  int n = 0;
+  long long n_nodes = 0, n_links = 0;
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  std::vector<SnakeParams> hprm;
+  std::vector<int> node_off, link_off;
+  std::vector<float> inv_mass_h;
+  // device
+  float4 *pos = nullptr, *vel = nullptr;
+  float2* press = nullptr;
+  float* lam = nullptr;
+  SnakeParams* prm = nullptr;
+  int *node_off_d = nullptr, *link_off_d = nullptr;
+  float* resid = nullptr;
+  int *iters = nullptr, *status = nullptr;
+  int4* items = nullptr;
+  int* order = nullptr;
+  int n_items = 0;
+  int npl_first[5] = {0, 0, 0, 0, 0};  // items of nodes-per-lane p are [first[p-1], first[p])
+  int npl_grid[4] = {0, 0, 0, 0};
+  cudaStream_t side[4] = {nullptr, nullptr, nullptr, nullptr};
+  cudaEvent_t ev_side[4] = {nullptr, nullptr, nullptr, nullptr};
+  float* ucmd = nullptr;
+  bool use_ucmd = false;
+  float* inv_mass_d = nullptr;
+  float* scratch3 = nullptr;  // [nodes * 6] staging for layout conversions
+  float* lam0 = nullptr;      // optional learned warm start
+  float* lam_log = nullptr;   // optional per-substep multiplier log
+  long long step_index = 0;
+  long long launches = 0;
+  std::map<int, int> layout;  // node count -> layout id
+  int grid = 0;
+  cudaGraphExec_t graph = nullptr;
+  int graph_steps = -1;
+  bool graph_dirty = true;
+};
+
+namespace {
+
+SimStatus validate_cfg(const SimConfig* c) {
+  if (!c) return fail(SIM_EINVAL, "null config");
+  if (!(c->dt > 0.0) || c->n_sub < 1 || c->iters < 0 || !(c->tol >= 0.f) || !(c->omega > 0.f) ||
+      c->warm < 0 || c->warm > 2)
+    return fail(SIM_EINVAL, "invalid config (dt > 0, n_sub >= 1, iters >= 0, tol >= 0, omega > 0, warm in 0..2)");
+  return SIM_OK;
+}
+
+int default_layout(int N) {
+  for (int G : {8, 16, 32}) {
+    if (G * 4 >= N) {
+      int npl = (N + G - 1) / G;
+      return layout_id(G, std::max(1, npl));
+    }
+  }
+  return -1;
+}
+
+SimStatus build_items(SimHandle* h, const std::map<int, int>* only_bucket = nullptr) {
+  // group snakes by node count, pack 32/G snakes per warp item, biggest work first;
+  // `only_bucket` restricts the items to the node counts it lists (autotuning)
+  std::map<int, std::vector<int>> buckets;
+  for (int s = 0; s < h->n; ++s) buckets[h->node_off[s + 1] - h->node_off[s]].push_back(s);
+  std::vector<int> order;
+  struct It { int off, cnt, lay; float cost; };
+  std::vector<It> its;
+  for (auto& kv : buckets) {
+    if (!h->layout.count(kv.first)) h->layout[kv.first] = default_layout(kv.first);
+    if (only_bucket && !only_bucket->count(kv.first)) continue;
+    const int lay = h->layout[kv.first];
+    if (lay < 0) return fail(SIM_EINVAL, "snake too long for the lane layouts (max 128 nodes)");
+    const int G = layout_lanes(lay), per = 32 / G;
+    for (size_t b = 0; b < kv.second.size(); b += per) {
+      It it;
+      it.off = (int)order.size();
+      it.cnt = (int)std::min<size_t>(per, kv.second.size() - b);
+      it.lay = lay;
+      it.cost = (float)layout_npl(lay);
+      for (int c = 0; c < it.cnt; ++c) order.push_back(kv.second[b + c]);
+      its.push_back(it);
+    }
+  }
+  // items ordered by nodes per lane (one kernel each), then by snake length inside
+  std::stable_sort(its.begin(), its.end(), [](const It& a, const It& b) {
+    return layout_npl(a.lay) < layout_npl(b.lay);
+  });
+  std::vector<int4> hitems(its.size());
+  for (size_t i = 0; i < its.size(); ++i) hitems[i] = make_int4(its[i].off, its[i].cnt, its[i].lay, 0);
+  if (h->items) cudaFree(h->items);
+  if (h->order) cudaFree(h->order);
+  h->items = nullptr; h->order = nullptr;
+  h->n_items = (int)hitems.size();
+  if (h->n_items > 0) {
+    CU(cudaMalloc(&h->items, hitems.size() * sizeof(int4)));
+    CU(cudaMalloc(&h->order, order.size() * sizeof(int)));
+    CU(cudaMemcpy(h->items, hitems.data(), hitems.size() * sizeof(int4), cudaMemcpyHostToDevice));
+    CU(cudaMemcpy(h->order, order.data(), order.size() * sizeof(int), cudaMemcpyHostToDevice));
+  }
+  for (int p = 0; p <= 4; ++p) h->npl_first[p] = 0;
+  for (size_t i = 0; i < its.size(); ++i) h->npl_first[layout_npl(its[i].lay)] = (int)i + 1;
+  for (int p = 1; p <= 4; ++p) h->npl_first[p] = std::max(h->npl_first[p], h->npl_first[p - 1]);
+  int dev = 0, sms = 0;
+  CU(cudaGetDevice(&dev));
+  CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  for (int p = 0; p < 4; ++p) {
+    int per_sm = 0;
+    CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kSolverKernels[p], 128, 0));
+    const int n = h->npl_first[p + 1] - h->npl_first[p];
+    const int need = (n + 3) / 4;
+    h->npl_grid[p] = n == 0 ? 0 : std::max(1, std::min(need, std::max(1, per_sm) * sms));
+  }
+  h->graph_dirty = true;
+  return SIM_OK;
+}
+
+SolverArgs make_args(SimHandle* h, int n_steps) {
+  SolverArgs A;
+  A.pos = h->pos; A.vel = h->vel; A.press = h->press; A.lam = h->lam; A.prm = h->prm;
+  A.node_off = h->node_off_d; A.link_off = h->link_off_d;
+  A.resid = h->resid; A.iters = h->iters; A.status = h->status;
+  A.items = h->items; A.order = h->order; A.n_items = h->n_items;
+  A.ucmd = h->use_ucmd ? h->ucmd : nullptr;
+  A.lam0 = (h->cfg.warm == SIM_WARM_LEARNED) ? h->lam0 : nullptr;
+  A.lam_log = h->lam_log;
+  A.step_index = h->step_index;
+  A.total_nodes = h->n_nodes;
+  A.n_steps = n_steps;
+  A.h_d = h->cfg.dt / h->cfg.n_sub;
+  A.h = (float)A.h_d;
+  A.n_sub = h->cfg.n_sub;
+  A.K = h->cfg.iters;
+  A.tol = h->cfg.tol;
+  A.omega = h->cfg.omega;
+  A.g[0] = h->cfg.gravity[0]; A.g[1] = h->cfg.gravity[1]; A.g[2] = h->cfg.gravity[2];
+  A.contact = h->cfg.contact;
+  A.warm = h->cfg.warm;
+  return A;
+}
+
+SimStatus launch_steps(SimHandle* h, int n_steps, cudaStream_t st) {
+  if (n_steps <= 0 || h->n_items == 0) return SIM_OK;
+  SolverArgs A = make_args(h, n_steps);
+  int kinds = 0;
+  for (int p = 0; p < 4; ++p) kinds += h->npl_grid[p] > 0;
+  bool fork = kinds > 1;
+  if (fork) CU(cudaEventRecord(h->ev_fork, st));
+  for (int p = 0; p < 4; ++p) {
+    if (h->npl_grid[p] == 0) continue;
+    SolverArgs B = A;
+    B.items = h->items + h->npl_first[p];
+    B.n_items = h->npl_first[p + 1] - h->npl_first[p];
+    cudaStream_t s = fork ? h->side[p] : st;
+    if (fork) CU(cudaStreamWaitEvent(s, h->ev_fork, 0));
+    kSolverKernels[p]<<<h->npl_grid[p], 128, 0, s>>>(B);
+    CU(cudaGetLastError());
+    h->launches += 1;
+    if (fork) {
+      CU(cudaEventRecord(h->ev_side[p], s));
+      CU(cudaStreamWaitEvent(st, h->ev_side[p], 0));
+    }
+  }
+  return SIM_OK;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ C-ABI
+extern "C" {
+
+const char* sim_last_error(void) { return g_err.c_str(); }
+
+SimStatus sim_create(const SimConfig* cfg, int n_snakes, const SnakeParams* params, void* stream,
+                     SimHandle** out) {
+  if (!out) return fail(SIM_EINVAL, "null output handle");
+  *out = nullptr;
+  SimStatus st = validate_cfg(cfg);
+  if (st != SIM_OK) return st;
+  if (n_snakes < 1 || !params) return fail(SIM_EINVAL, "n_snakes < 1 or null params");
+  for (int s = 0; s < n_snakes; ++s) {
+    const SnakeParams& p = params[s];
+    long long N = (long long)p.n_links * p.seg_per_link + 1;
+    if (p.n_links < 1 || p.seg_per_link < 1 || p.n_fixed < 0 || p.n_fixed > N || !(p.L0 > 0.f) ||
+        !(p.mass > 0.f) || !(p.alpha_s >= 0.f) || !(p.alpha_b >= 0.f) || !(p.tau_inf > 0.f) ||
+        !(p.tau_def > 0.f) || !(p.mu >= 0.f) || !(p.damping >= 0.f))
+      return fail(SIM_EINVAL, "invalid parameters of snake " + std::to_string(s));
+    if (N > 128) return fail(SIM_EINVAL, "snake " + std::to_string(s) + " has more than 128 nodes");
+  }
+  SimHandle* h = new SimHandle();
+  h->cfg = *cfg;
+  h->n = n_snakes;
+  h->stream = (cudaStream_t)stream;
+  h->hprm.assign(params, params + n_snakes);
+  h->node_off.resize(n_snakes + 1);
+  h->link_off.resize(n_snakes + 1);
+  h->node_off[0] = h->link_off[0] = 0;
+  for (int s = 0; s < n_snakes; ++s) {
+    h->node_off[s + 1] = h->node_off[s] + params[s].n_links * params[s].seg_per_link + 1;
+    h->link_off[s + 1] = h->link_off[s] + params[s].n_links;
+  }
+  h->n_nodes = h->node_off[n_snakes];
+  h->n_links = h->link_off[n_snakes];
+  auto cleanup = [&](SimStatus s) { sim_destroy(h); return s; };
+  // host-side initial pose: straight along yaw0 from (x0, y0, z0), at rest
+  std::vector<float4> pos(h->n_nodes), vel(h->n_nodes, make_float4(0.f, 0.f, 0.f, 0.f));
+  h->inv_mass_h.resize(h->n_nodes);
+  for (int s = 0; s < n_snakes; ++s) {
+    const SnakeParams& p = params[s];
+    const double c = std::cos((double)p.yaw0), sn = std::sin((double)p.yaw0);
+    for (int i = 0; i < h->node_off[s + 1] - h->node_off[s]; ++i) {
+      const double d = (double)i * p.L0;
+      const float w = (i < p.n_fixed) ? 0.f : 1.0f / p.mass;
+      pos[h->node_off[s] + i] = make_float4((float)(p.x0 + d * c), (float)(p.y0 + d * sn), p.z0, w);
+      h->inv_mass_h[h->node_off[s] + i] = w;
+    }
+  }
+  cudaError_t e;
+#define ALLOC(ptr, bytes)                                                     \
+  e = cudaMalloc((void**)&(ptr), (bytes));                                    \
+  if (e != cudaSuccess) return cleanup(fail(SIM_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e)));
+  ALLOC(h->pos, h->n_nodes * sizeof(float4));
+  ALLOC(h->vel, h->n_nodes * sizeof(float4));
+  ALLOC(h->press, h->n_links * sizeof(float2));
+  ALLOC(h->lam, h->n_nodes * 6 * sizeof(float));
+  ALLOC(h->prm, n_snakes * sizeof(SnakeParams));
+  ALLOC(h->node_off_d, (n_snakes + 1) * sizeof(int));
+  ALLOC(h->link_off_d, (n_snakes + 1) * sizeof(int));
+  ALLOC(h->resid, n_snakes * sizeof(float));
+  ALLOC(h->iters, n_snakes * sizeof(int));
+  ALLOC(h->status, n_snakes * sizeof(int));
+  ALLOC(h->ucmd, std::max<long long>(1, h->n_links) * sizeof(float));
+  ALLOC(h->inv_mass_d, h->n_nodes * sizeof(float));
+  ALLOC(h->scratch3, h->n_nodes * 6 * sizeof(float));
+#undef ALLOC
+#define CUC(call)                                                                         \
+  e = (call);                                                                             \
+  if (e != cudaSuccess) return cleanup(fail(SIM_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e)));
+  CUC(cudaMemcpy(h->pos, pos.data(), h->n_nodes * sizeof(float4), cudaMemcpyHostToDevice));
+  CUC(cudaMemcpy(h->vel, vel.data(), h->n_nodes * sizeof(float4), cudaMemcpyHostToDevice));
+  CUC(cudaMemset(h->press, 0, h->n_links * sizeof(float2)));
+  CUC(cudaMemset(h->lam, 0, h->n_nodes * 6 * sizeof(float)));
+  CUC(cudaMemcpy(h->prm, params, n_snakes * sizeof(SnakeParams), cudaMemcpyHostToDevice));
+  CUC(cudaMemcpy(h->node_off_d, h->node_off.data(), (n_snakes + 1) * sizeof(int), cudaMemcpyHostToDevice));
+  CUC(cudaMemcpy(h->link_off_d, h->link_off.data(), (n_snakes + 1) * sizeof(int), cudaMemcpyHostToDevice));
+  CUC(cudaMemset(h->resid, 0, n_snakes * sizeof(float)));
+  CUC(cudaMemset(h->iters, 0, n_snakes * sizeof(int)));
+  CUC(cudaMemset(h->status, 0, n_snakes * sizeof(int)));
+  CUC(cudaMemcpy(h->inv_mass_d, h->inv_mass_h.data(), h->n_nodes * sizeof(float), cudaMemcpyHostToDevice));
+  CUC(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+  CUC(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+  CUC(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
+  for (int p = 0; p < 4; ++p) {
+    CUC(cudaStreamCreateWithFlags(&h->side[p], cudaStreamNonBlocking));
+    CUC(cudaEventCreateWithFlags(&h->ev_side[p], cudaEventDisableTiming));
+  }
+#undef CUC
+  st = build_items(h);
+  if (st != SIM_OK) return cleanup(st);
+  *out = h;
+  return SIM_OK;
+}
+
+SimStatus sim_set_config(SimHandle* h, const SimConfig* cfg) {
+  if (!h) return fail(SIM_EINVAL, "null handle");
+  SimStatus st = validate_cfg(cfg);
+  if (st != SIM_OK) return st;
+  h->cfg = *cfg;
+  h->graph_dirty = true;
+  return SIM_OK;
+}
+
+SimStatus sim_set_pressure(SimHandle* h, const float* u, int is_device) {
+  if (!h) return fail(SIM_EINVAL, "null handle");
+  if (!u) { h->use_ucmd = false; h->graph_dirty = true; return SIM_OK; }
+  CU(cudaMemcpyAsync(h->ucmd, u, h->n_links * sizeof(float),
+                     is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
+  if (!is_device) CU(cudaStreamSynchronize(h->stream));
+  if (!h->use_ucmd) h->graph_dirty = true;
+  h->use_ucmd = true;
+  return SIM_OK;
+}
+
+SimStatus sim_step(SimHandle* h, int n_steps) {
+  if (!h) return fail(SIM_EINVAL, "null handle");
+  if (n_steps < 0) return fail(SIM_EINVAL, "n_steps < 0");
+  if (h->cfg.warm == SIM_WARM_LEARNED && !h->lam0)
+    return fail(SIM_EINVAL, "learned warm start requested but no warm-start multipliers were provided");
+  SimStatus st = launch_steps(h, n_steps, h->stream);
+  if (st != SIM_OK) return st;
+  h->step_index += n_steps;
+  return SIM_OK;
+}
+
+SimStatus sim_step_graph(SimHandle* h, int n_steps) {
+  if (!h) return fail(SIM_EINVAL, "null handle");
+  if (n_steps < 0) return fail(SIM_EINVAL, "n_steps < 0");
+  // The captured kernel reads its step counter from the launch arguments, so the graph
+  // is re-instantiated whenever the counter or the configuration changes; the update
+  // path below patches only the arguments of the existing kernel node.
+  CU(cudaEventRecord(h->ev_fork, h->stream));
+  CU(cudaStreamWaitEvent(h->cap_stream, h->ev_fork, 0));
+  cudaGraph_t g = nullptr;
+  CU(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+  long long launches0 = h->launches;
+  SimStatus st = launch_steps(h, n_steps, h->cap_stream);
+  cudaError_t ce = cudaStreamEndCapture(h->cap_stream, &g);
+  if (st != SIM_OK) { if (g) cudaGraphDestroy(g); return st; }
+  if (ce != cudaSuccess) return fail(SIM_ECUDA, std::string("capture: ") + cudaGetErrorString(ce));
+  bool updated = false;
+  if (h->graph && !h->graph_dirty && h->graph_steps == n_steps) {
+    cudaGraphExecUpdateResultInfo info;
+    if (cudaGraphExecUpdate(h->graph, g, &info) == cudaSuccess) updated = true;
+    else cudaGetLastError();
+  }
+  if (!updated) {
+    if (h->graph) cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+    ce = cudaGraphInstantiate(&h->graph, g, 0);
+    if (ce != cudaSuccess) { cudaGraphDestroy(g); return fail(SIM_ECUDA, std::string("instantiate: ") + cudaGetErrorString(ce)); }
+  }
+  cudaGraphDestroy(g);
+  h->graph_steps = n_steps;
+  h->graph_dirty = false;
+  CU(cudaGraphLaunch(h->graph, h->cap_stream));
+  CU(cudaEventRecord(h->ev_join, h->cap_stream));
+  CU(cudaStreamWaitEvent(h->stream, h->ev_join, 0));
+  (void)launches0;
+  h->step_index += n_steps;
+  return SIM_OK;
+}
+
+SimStatus sim_get_state(SimHandle* h, float* pos, float* vel, float* press, float* resid,
+                        int32_t* iters, int is_device) {
+  if (!h) return fail(SIM_EINVAL, "null handle");
+  const long long n = h->n_nodes;
+  const int blocks = (int)((n + 255) / 256);
+  auto kind = is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  if (pos) {
+    float* dst = is_device ? pos : h->scratch3;
+    pack_xyz_kernel<<<blocks, 256, 0, h->stream>>>(h->pos, dst, n);
+    CU(cudaGetLastError());
+    if (!is_device) CU(cudaMemcpyAsync(pos, h->scratch3, n * 3 * sizeof(float), kind, h->stream));
+    if (!is_device) CU(cudaStreamSynchronize(h->stream));
+  }
+  if (vel) {
+    float* dst = is_device ? vel : h->scratch3;
+    pack_xyz_kernel<<<blocks, 256, 0, h->stream>>>(h->vel, dst, n);
+    CU(cudaGetLastError());
+    if (!is_device) CU(cudaMemcpyAsync(vel, h->scratch3, n * 3 * sizeof(float), kind, h->stream));
+    if (!is_device) CU(cudaStreamSynchronize(h->stream));
+  }
+  if (press) CU(cudaMemcpyAsync(press, h->press, h->n_links * sizeof(float2), kind, h->stream));
+  if (resid) CU(cudaMemcpyAsync(resid, h->resid, h->n * sizeof(float), kind, h->stream));
+  if (iters) CU(cudaMemcpyAsync(iters, h->iters, h->n * sizeof(int), kind, h->stream));
+  if (!is_device) CU(cudaStreamSynchronize(h->stream));
+  return SIM_OK;
+}
+
+SimStatus sim_set_state(SimHandle* h, const float* pos, const float* vel, const float* press,
+                        const float* lam, int is_device) {
+  if (!h) return fail(SIM_EINVAL, "null handle");
+  const long long n = h->n_nodes;
+  const int blocks = (int)((n + 255) / 256);
+  auto kind = is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  if (pos) {
+    CU(cudaMemcpyAsync(h->scratch3, pos, n * 3 * sizeof(float), kind, h->stream));
+    unpack_xyz_kernel<<<blocks, 256, 0, h->stream>>>(h->scratch3, h->pos, n, h->inv_mass_d);
+    CU(cudaGetLastError());
+    CU(cudaStreamSynchronize(h->stream));
+  }
+  if (vel) {
+    CU(cudaMemcpyAsync(h->scratch3, vel, n * 3 * sizeof(float), kind, h->stream));
+    unpack_xyz_kernel<<<blocks, 256, 0, h->stream>>>(h->scratch3, h->vel, n, nullptr);
+    CU(cudaGetLastError());
+    CU(cudaStreamSynchronize(h->stream));
+  }
+  if (press) CU(cudaMemcpyAsync(h->press, press, h->n_links * sizeof(float2), kind, h->stream));
+  if (lam) CU(cudaMemcpyAsync(h->lam, lam, n * 6 * sizeof(float), kind, h->stream));
+  CU(cudaStreamSynchronize(h->stream));
+  return SIM_OK;
+}
+
+SimStatus sim_get_lambda(SimHandle* h, float* lam, int is_device) {
+  if (!h || !lam) return fail(SIM_EINVAL, "null handle or buffer");
+  CU(cudaMemcpyAsync(lam, h->lam, h->n_nodes * 6 * sizeof(float),
+                     is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream));
+  if (!is_device) CU(cudaStreamSynchronize(h->stream));
+  return SIM_OK;
+}
+
+SimStatus sim_get_info(SimHandle* h, int64_t* n_nodes, int64_t* n_links, int32_t* n_snakes,
+                       int64_t* step_index) {
+  if (!h) return fail(SIM_EINVAL, "null handle");
+  if (n_nodes) *n_nodes = h->n_nodes;
+  if (n_links) *n_links = h->n_links;
+  if (n_snakes) *n_snakes = h->n;
+  if (step_index) *step_index = h->step_index;
+  return SIM_OK;
+}
+
+SimStatus sim_set_step_index(SimHandle* h, int64_t step_index) {
+  if (!h) return fail(SIM_EINVAL, "null handle");
+  h->step_index = step_index;
+  return SIM_OK;
+}
+
+SimStatus sim_device_state(SimHandle* h, void** pos4, void** vel4, void** press2, void** lam) {
+  if (!h) return fail(SIM_EINVAL, "null handle");
+  if (pos4) *pos4 = h->pos;
+  if (vel4) *vel4 = h->vel;
+  if (press2) *press2 = h->press;
+  if (lam) *lam = h->lam;
+  return SIM_OK;
+}
+
+SimStatus sim_get_status(SimHandle* h, int32_t* status) {
+  if (!h) return fail(SIM_EINVAL, "null handle");
+  std::vector<int> s(h->n);
+  CU(cudaMemcpyAsync(s.data(), h->status, h->n * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  CU(cudaStreamSynchronize(h->stream));
+  SimStatus worst = SIM_OK;
+  for (int i = 0; i < h->n; ++i) {
+    if (status) status[i] = s[i];
+    if (s[i] == SIM_ENAN) worst = SIM_ENAN;
+    else if (s[i] == SIM_NOT_CONVERGED && worst == SIM_OK) worst = SIM_NOT_CONVERGED;
+  }
+  return worst;
+}
+
+SimStatus sim_get_layout(SimHandle* h, int nodes, int32_t* lanes, int32_t* npl) {
+  if (!h) return fail(SIM_EINVAL, "null handle");
+  auto it = h->layout.find(nodes);
+  if (lanes) *lanes = it == h->layout.end() ? 0 : layout_lanes(it->second);
+  if (npl) *npl = it == h->layout.end() ? 0 : layout_npl(it->second);
+  return SIM_OK;
+}
+
+SimStatus sim_set_layout(SimHandle* h, int nodes, int lanes, int npl) {
+  if (!h) return fail(SIM_EINVAL, "null handle");
+  if (!(lanes == 8 || lanes == 16 || lanes == 32) || npl < 1 || npl > 4 || lanes * npl < nodes)
+    return fail(SIM_EINVAL, "layout needs lanes in {8,16,32}, nodes_per_lane in 1..4, lanes*npl >= nodes");
+  h->layout[nodes] = layout_id(lanes, npl);
+  return build_items(h);
+}
+
+SimStatus sim_autotune(SimHandle* h, int n_steps) {
+  if (!h) return fail(SIM_EINVAL, "null handle");
+  if (n_steps < 1) return fail(SIM_EINVAL, "n_steps < 1");
+  // save the state, time every admissible layout of every bucket alone, restore
+  const long long n = h->n_nodes;
+  float4 *p0 = nullptr, *v0 = nullptr;
+  float2* pr0 = nullptr;
+  float* l0 = nullptr;
+  CU(cudaMalloc(&p0, n * sizeof(float4)));
+  CU(cudaMalloc(&v0, n * sizeof(float4)));
+  CU(cudaMalloc(&pr0, h->n_links * sizeof(float2)));
+  CU(cudaMalloc(&l0, n * 6 * sizeof(float)));
+  auto save = [&]() -> SimStatus {
+    CU(cudaMemcpyAsync(p0, h->pos, n * sizeof(float4), cudaMemcpyDeviceToDevice, h->stream));
+    CU(cudaMemcpyAsync(v0, h->vel, n * sizeof(float4), cudaMemcpyDeviceToDevice, h->stream));
+    CU(cudaMemcpyAsync(pr0, h->press, h->n_links * sizeof(float2), cudaMemcpyDeviceToDevice, h->stream));
+    CU(cudaMemcpyAsync(l0, h->lam, n * 6 * sizeof(float), cudaMemcpyDeviceToDevice, h->stream));
+    return SIM_OK;
+  };
+  auto restore = [&]() -> SimStatus {
+    CU(cudaMemcpyAsync(h->pos, p0, n * sizeof(float4), cudaMemcpyDeviceToDevice, h->stream));
+    CU(cudaMemcpyAsync(h->vel, v0, n * sizeof(float4), cudaMemcpyDeviceToDevice, h->stream));
+    CU(cudaMemcpyAsync(h->press, pr0, h->n_links * sizeof(float2), cudaMemcpyDeviceToDevice, h->stream));
+    CU(cudaMemcpyAsync(h->lam, l0, n * 6 * sizeof(float), cudaMemcpyDeviceToDevice, h->stream));
+    return SIM_OK;
+  };
+  SimStatus st = save();
+  cudaEvent_t a, b;
+  CU(cudaEventCreate(&a));
+  CU(cudaEventCreate(&b));
+  std::map<int, int> best = h->layout;
+  std::vector<int> sizes;
+  for (auto& kv : h->layout) sizes.push_back(kv.first);
+  for (int N : sizes) {
+    float best_ms = 1e30f;
+    for (int G : {8, 16, 32}) {
+      for (int npl = 1; npl <= 4; ++npl) {
+        if (G * npl < N || (npl > 1 && G * (npl - 1) >= N)) continue;  // no empty lanes column
+        std::map<int, int> one;
+        one[N] = layout_id(G, npl);
+        std::map<int, int> saved = h->layout;
+        h->layout[N] = layout_id(G, npl);
+        st = build_items(h, &one);
+        if (st != SIM_OK) break;
+        float ms = 0.f;
+        for (int rep = 0; rep < 2 && st == SIM_OK; ++rep) {
+          if ((st = restore()) != SIM_OK) break;
+          CU(cudaEventRecord(a, h->stream));
+          st = launch_steps(h, n_steps, h->stream);
+          CU(cudaEventRecord(b, h->stream));
+          CU(cudaEventSynchronize(b));
+          CU(cudaEventElapsedTime(&ms, a, b));
+        }
+        h->layout = saved;
+        if (st != SIM_OK) break;
+        if (ms < best_ms) { best_ms = ms; best[N] = layout_id(G, npl); }
+      }
+      if (st != SIM_OK) break;
+    }
+    if (st != SIM_OK) break;
+  }
+  if (st == SIM_OK) st = restore();
+  CU(cudaStreamSynchronize(h->stream));
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  cudaFree(p0); cudaFree(v0); cudaFree(pr0); cudaFree(l0);
+  if (st != SIM_OK) return st;
+  h->layout = best;
+  return build_items(h);
+}
+
+SimStatus sim_launch_count(SimHandle* h, int64_t* launches) {
+  if (!h || !launches) return fail(SIM_EINVAL, "null handle or output");
+  *launches = h->launches;
+  return SIM_OK;
+}
+
+SimStatus sim_destroy(SimHandle* h) {
+  if (!h) return SIM_OK;
+  cudaStreamSynchronize(h->stream);
+  if (h->graph) cudaGraphExecDestroy(h->graph);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
+  for (int p = 0; p < 4; ++p) {
+    if (h->side[p]) cudaStreamDestroy(h->side[p]);
+    if (h->ev_side[p]) cudaEventDestroy(h->ev_side[p]);
+  }
+  void* ptrs[] = {h->pos, h->vel, h->press, h->lam, h->prm, h->node_off_d, h->link_off_d, h->resid,
+                  h->iters, h->status, h->items, h->order, h->ucmd, h->inv_mass_d, h->scratch3,
+                  h->lam0, h->lam_log};
+  for (void* p : ptrs) if (p) cudaFree(p);
+  delete h;
+  return SIM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,456 @@
+// Substep solver of the soft-snake chain (sm_103a), register-resident.
+//
+// One snake is owned by a group of G lanes of a warp (G = 8, 16 or 32); lane q of the
+// group owns the NPL consecutive nodes q*NPL .. q*NPL+NPL-1 and keeps their
+// substep-start position, displacement within the substep, velocity, the six
+// multipliers of the rows they own (stretch to the next node, yaw and pitch bend,
+// contact, friction x/y), chamber pressures and rest angles in registers for all
+// substeps and env-steps of a launch.
+//
+// Positions are held as x = x_s + d: x_s (the substep-start position, up to metres from
+// the origin) is fixed during the substep and d (a fraction of a millimetre) collects
+// the Jacobi corrections.  In FP32 a correction added to x directly is rounded to
+// ulp(|x|) ~ 6e-8 m and the late, small corrections are lost, which stalls the
+// residual near 1e-4; added to d they keep ~1e-11 m.  Segment vectors are formed as
+// (x_s,b - x_s,a) + (d_b - d_a), contact heights as (z_s - r) + d_z, friction slips as d.  Neighbour
+// positions and the gradient-times-multiplier contributions that cross a lane boundary
+// move by warp shuffles; nothing touches shared or global memory inside the Jacobi loop.
+//
+// The arithmetic of every step cites the paper (Gasoto et al., arXiv 1904.02833):
+//   gait              Eq. 9 (Sec. V-A)
+//   chambers          antagonistic pair, Sec. III; first-order latency (Sec. V-A's
+//                     latency model replaced by exact exponential relaxation)
+//   rest angle        Eq. 3-4 with the inextensible centre layer of Sec. V
+//   rows              c + E lambda = 0 (Sec. IV), contact Eq. 7, Coulomb cone (Sec. IV)
+//   Jacobi relaxation Eq. 8 with its diagonal (Sec. IV-D)
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "internal.h"
+
+namespace snakesim {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+struct Seg {  // derived quantities of the segment from node i to node i+1
+  float ex, ey, ez;   // edge vector
+  float len;          // |e|
+  float nx, ny, nz;   // e / |e|
+  float gyx, gyy;     // L0 d(heading)/de = L0 (-e_y, e_x) / |e_h|^2
+  float gpx, gpy, gpz;// L0 d(elevation)/de = L0 (-e_z e_x, -e_z e_y, |e_h|^2) / (|e|^2 |e_h|)
+  float beta;         // elevation atan2(e_z, |e_h|) = asin(e_z / |e|)
+};
+
+__device__ __forceinline__ Seg make_seg(float ex, float ey, float ez, float L0) {
+  Seg s;
+  s.ex = ex; s.ey = ey; s.ez = ez;
+  const float h2 = s.ex * s.ex + s.ey * s.ey;
+  const float l2 = h2 + s.ez * s.ez;
+  const float il = rsqrtf(l2);
+  s.len = l2 * il;
+  s.nx = s.ex * il; s.ny = s.ey * il; s.nz = s.ez * il;
+  const float ih2 = 1.0f / h2;
+  const float ih = rsqrtf(h2);
+  s.gyx = -L0 * s.ey * ih2;
+  s.gyy = L0 * s.ex * ih2;
+  const float f = L0 * il * il * ih;
+  s.gpx = -s.ez * s.ex * f;
+  s.gpy = -s.ez * s.ey * f;
+  s.gpz = h2 * f;
+  s.beta = atan2f(s.ez, h2 * ih);
+  return s;
+}
+
+template <int G>
+__device__ __forceinline__ float group_max(float r) {
+#pragma unroll
+  for (int off = G / 2; off >= 1; off >>= 1) r = fmaxf(r, __shfl_xor_sync(kFull, r, off, G));
+  return r;
+}
+
+// Per-group constants of one snake.
+struct SnakeK {
+  int N, seg, nfix, L, nb, lb;
+  float L0, inv_m, at_s, at_b, mu, radius, gain, e_inf, e_def, damp_over_h;
+};
+
+// One pass over the rows at the current positions and multipliers.
+//   WARM = false: Jacobi pass.  Evaluates every row at (x^k, lambda^k), returns the
+//     group's normalised residual, and (unless `apply` comes back false) replaces
+//     lambda by its relaxed update and moves every free node by w_i sum_j grad_i c_j d_j.
+//   WARM = true: warm-start pass.  Uses d_j = lambda_j (zeroing rows that do not exist
+//     or touch no free node) and applies it, so that M (x - x~) = J^T lambda.
+// `stop_at` returns the group's stop decision (residual <= tol or cap reached).
+template <int NPL, int G, bool WARM>
+__device__ __forceinline__ float row_pass(const SnakeK& S, const SolverArgs& A, int q,
+                                          bool live, int kiter, const float (&xs)[NPL][3],
+                                          float (&dx)[NPL][3], const float (&xsl)[3],
+                                          const float (&xsr)[3], float (&lam)[NPL][6],
+                                          const float (&th)[NPL], bool& stop) {
+  const float L0 = S.L0;
+  // neighbour displacements across the lane boundary
+  float dxl[3], dxr[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    dxl[d] = __shfl_up_sync(kFull, dx[NPL - 1][d], 1, G);
+    dxr[d] = __shfl_down_sync(kFull, dx[0][d], 1, G);
+  }
+  float acc[NPL][3];
+  float dl[NPL][6];
+  float accL[3] = {0.f, 0.f, 0.f}, accR[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+  for (int j = 0; j < NPL; ++j) {
+    acc[j][0] = acc[j][1] = acc[j][2] = 0.f;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) dl[j][k] = 0.f;
+  }
+  float r = 0.f;
+  const int i0 = q * NPL;
+  // segment i0-1 (from the left neighbour's last node to my first node)
+  Seg sp;
+  {
+    const bool ok = live && i0 >= 1 && i0 <= S.N - 1;
+    if (ok) sp = make_seg((xs[0][0] - xsl[0]) + (dx[0][0] - dxl[0]),
+                          (xs[0][1] - xsl[1]) + (dx[0][1] - dxl[1]),
+                          (xs[0][2] - xsl[2]) + (dx[0][2] - dxl[2]), L0);
+    else sp = make_seg(1.f, 0.f, 0.f, L0);
+  }
+#pragma unroll
+  for (int j = 0; j < NPL; ++j) {
+    const int i = i0 + j;
+    const bool act = live && i < S.N;
+    const float wi = (i < S.nfix) ? 0.f : S.inv_m;
+    const float wl = (i - 1 < S.nfix) ? 0.f : S.inv_m;
+    const float wr = (i + 1 < S.nfix) ? 0.f : S.inv_m;
+    // segment i (my node j to node i+1)
+    float bsx, bsy, bsz, bdx, bdy, bdz;
+    if (j + 1 < NPL) {
+      bsx = xs[j + 1][0]; bsy = xs[j + 1][1]; bsz = xs[j + 1][2];
+      bdx = dx[j + 1][0]; bdy = dx[j + 1][1]; bdz = dx[j + 1][2];
+    } else {
+      bsx = xsr[0]; bsy = xsr[1]; bsz = xsr[2];
+      bdx = dxr[0]; bdy = dxr[1]; bdz = dxr[2];
+    }
+    const bool has_seg = act && i + 1 <= S.N - 1;
+    Seg sc = has_seg ? make_seg((bsx - xs[j][0]) + (bdx - dx[j][0]), (bsy - xs[j][1]) + (bdy - dx[j][1]),
+                                (bsz - xs[j][2]) + (bdz - dx[j][2]), L0)
+                     : make_seg(1.f, 0.f, 0.f, L0);
+    float* tl = (j > 0) ? acc[j - 1] : accL;          // node i-1
+    float* tr = (j + 1 < NPL) ? acc[j + 1] : accR;    // node i+1
+    // ---- stretch (i, i+1): c = |e| - L0 (Eq. 3 with a constant rest length)
+    if (has_seg) {
+      const float c = sc.len - L0;
+      const float wg = wi + wr;
+      if (wg > 0.f) {
+        const float l = WARM ? 0.f : lam[j][0];
+        float d;
+        if (WARM) d = lam[j][0];
+        else {
+          r = fmaxf(r, fabsf(c + S.at_s * l) / L0);
+          d = A.omega * (-c - S.at_s * l) / (wg + S.at_s);
+        }
+        dl[j][0] = d;
+        acc[j][0] -= sc.nx * d; acc[j][1] -= sc.ny * d; acc[j][2] -= sc.nz * d;
+        tr[0] += sc.nx * d; tr[1] += sc.ny * d; tr[2] += sc.nz * d;
+      }
+    }
+    // ---- yaw and pitch bend centred on node i (rows in length units: L0 x angle)
+    if (act && i >= 1 && i <= S.N - 2) {
+      // yaw: L0 (atan2(z . (e1 x e2), e1_h . e2_h) - theta_rest)
+      {
+        const float cz = sp.ex * sc.ey - sp.ey * sc.ex;
+        const float dh = sp.ex * sc.ex + sp.ey * sc.ey;
+        const float c = L0 * (atan2f(cz, dh) - th[j]);
+        const float g0x = sp.gyx, g0y = sp.gyy;                   // node i-1
+        const float g1x = -sp.gyx - sc.gyx, g1y = -sp.gyy - sc.gyy; // node i
+        const float g2x = sc.gyx, g2y = sc.gyy;                   // node i+1
+        const float wg = wl * (g0x * g0x + g0y * g0y) + wi * (g1x * g1x + g1y * g1y) +
+                         wr * (g2x * g2x + g2y * g2y);
+        if (wg > 0.f) {
+          float d;
+          if (WARM) d = lam[j][1];
+          else {
+            const float l = lam[j][1];
+            r = fmaxf(r, fabsf(c + S.at_b * l) / L0);
+            d = A.omega * (-c - S.at_b * l) / (wg + S.at_b);
+          }
+          dl[j][1] = d;
+          tl[0] += g0x * d; tl[1] += g0y * d;
+          acc[j][0] += g1x * d; acc[j][1] += g1y * d;
+          tr[0] += g2x * d; tr[1] += g2y * d;
+        }
+      }
+      // pitch: L0 (elevation(e2) - elevation(e1))
+      {
+        const float c = L0 * (sc.beta - sp.beta);
+        const float g0x = sp.gpx, g0y = sp.gpy, g0z = sp.gpz;
+        const float g1x = -sp.gpx - sc.gpx, g1y = -sp.gpy - sc.gpy, g1z = -sp.gpz - sc.gpz;
+        const float g2x = sc.gpx, g2y = sc.gpy, g2z = sc.gpz;
+        const float wg = wl * (g0x * g0x + g0y * g0y + g0z * g0z) +
+                         wi * (g1x * g1x + g1y * g1y + g1z * g1z) +
+                         wr * (g2x * g2x + g2y * g2y + g2z * g2z);
+        if (wg > 0.f) {
+          float d;
+          if (WARM) d = lam[j][2];
+          else {
+            const float l = lam[j][2];
+            r = fmaxf(r, fabsf(c + S.at_b * l) / L0);
+            d = A.omega * (-c - S.at_b * l) / (wg + S.at_b);
+          }
+          dl[j][2] = d;
+          tl[0] += g0x * d; tl[1] += g0y * d; tl[2] += g0z * d;
+          acc[j][0] += g1x * d; acc[j][1] += g1y * d; acc[j][2] += g1z * d;
+          tr[0] += g2x * d; tr[1] += g2y * d; tr[2] += g2z * d;
+        }
+      }
+    }
+    // ---- ground contact (Eq. 7, z - r >= 0) and Coulomb friction pair
+    if (act && A.contact && wi > 0.f) {
+      const float ln = lam[j][3];
+      const float cn = (xs[j][2] - S.radius) + dx[j][2];
+      const float ux = dx[j][0], uy = dx[j][1];
+      float dn, dx, dy;
+      if (WARM) { dn = ln; dx = lam[j][4]; dy = lam[j][5]; }
+      else {
+        // residuals: Fischer-Burmeister on (c_n, w lambda_n); natural map of the disc
+        const float b = wi * ln;
+        r = fmaxf(r, fabsf(cn + b - sqrtf(cn * cn + b * b)) / L0);
+        const float rho = wi * S.mu * ln;
+        const float ax = wi * lam[j][4], ay = wi * lam[j][5];
+        float px = ax - ux, py = ay - uy;
+        const float pn = sqrtf(px * px + py * py);
+        if (pn > rho) {
+          if (rho > 0.f) { px *= rho / pn; py *= rho / pn; } else { px = 0.f; py = 0.f; }
+        }
+        r = fmaxf(r, sqrtf((ax - px) * (ax - px) + (ay - py) * (ay - py)) / L0);
+        // contact: lambda_n <- max(0, lambda_n + omega (-c_n / w))
+        const float nl = fmaxf(0.f, ln + A.omega * (-cn / wi));
+        dn = nl - ln;
+        // friction: relaxed update projected onto |lambda_t| <= mu lambda_n (current
+        // iterate's lambda_n)
+        float tx = lam[j][4] + A.omega * (-ux / wi);
+        float ty = lam[j][5] + A.omega * (-uy / wi);
+        const float rad = S.mu * ln;
+        const float n2 = tx * tx + ty * ty;
+        if (n2 > rad * rad) {
+          if (rad <= 0.f) { tx = 0.f; ty = 0.f; }
+          else { const float sc2 = rad / sqrtf(n2); tx *= sc2; ty *= sc2; }
+        }
+        dx = tx - lam[j][4]; dy = ty - lam[j][5];
+      }
+      dl[j][3] = dn; dl[j][4] = dx; dl[j][5] = dy;
+      acc[j][2] += dn;
+      acc[j][0] += dx;
+      acc[j][1] += dy;
+    }
+    sp = sc;
+  }
+  if (!WARM) {
+    if (!(r <= 3.0e38f)) r = INFINITY;  // NaN -> inf so that the max keeps it
+    r = group_max<G>(r);
+    stop = (r <= A.tol) || (kiter >= A.K);
+  } else {
+    stop = false;
+  }
+  // contributions that cross lane boundaries
+  float fromR[3], fromL[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    fromR[d] = __shfl_down_sync(kFull, accL[d], 1, G);  // right lane's rows -> my last node
+    fromL[d] = __shfl_up_sync(kFull, accR[d], 1, G);    // left lane's rows -> my first node
+  }
+  if (live && !stop) {
+#pragma unroll
+    for (int j = 0; j < NPL; ++j) {
+      const int i = i0 + j;
+      if (i >= S.N) continue;
+      float ax = acc[j][0], ay = acc[j][1], az = acc[j][2];
+      if (j == 0 && q > 0) { ax += fromL[0]; ay += fromL[1]; az += fromL[2]; }
+      if (j == NPL - 1 && q < G - 1) { ax += fromR[0]; ay += fromR[1]; az += fromR[2]; }
+      const float wi = (i < S.nfix) ? 0.f : S.inv_m;
+      dx[j][0] += wi * ax; dx[j][1] += wi * ay; dx[j][2] += wi * az;
+#pragma unroll
+      for (int k = 0; k < 6; ++k) lam[j][k] = WARM ? dl[j][k] : lam[j][k] + dl[j][k];
+    }
+  }
+  return r;
+}
+
+// Advances the snake owned by this lane group by A.n_steps env-steps.
+template <int NPL, int G>
+__device__ void run_group(const SolverArgs& A, int snake, bool valid) {
+  const int lane = threadIdx.x & 31;
+  const int q = lane & (G - 1);
+  SnakeK S;
+  SnakeParams P;
+  if (valid) P = A.prm[snake];
+  else { P = SnakeParams(); P.n_links = 0; P.seg_per_link = 1; P.mass = 1.f; P.L0 = 1.f;
+         P.tau_inf = 1.f; P.tau_def = 1.f; }
+  const float h = A.h;
+  S.N = valid ? P.n_links * P.seg_per_link + 1 : 0;
+  S.seg = P.seg_per_link; S.nfix = P.n_fixed; S.L = P.n_links;
+  S.nb = valid ? A.node_off[snake] : 0;
+  S.lb = valid ? A.link_off[snake] : 0;
+  S.L0 = P.L0; S.inv_m = 1.0f / P.mass;
+  S.at_s = P.alpha_s / (h * h); S.at_b = P.alpha_b / (h * h);
+  S.mu = P.mu; S.radius = P.radius; S.gain = P.gain;
+  S.e_inf = expf(-h / P.tau_inf); S.e_def = expf(-h / P.tau_def);
+  S.damp_over_h = expf(-P.damping * h) / h;
+
+  // x = xs + dx; between substeps dx holds the last substep's displacement
+  float xs[NPL][3], dx[NPL][3], v[NPL][3], lam[NPL][6], pR[NPL], pL[NPL], th[NPL];
+#pragma unroll
+  for (int j = 0; j < NPL; ++j) {
+    const int i = q * NPL + j;
+    th[j] = 0.f;
+    dx[j][0] = dx[j][1] = dx[j][2] = 0.f;
+    if (valid && i < S.N) {
+      const float4 p = A.pos[S.nb + i];
+      const float4 u = A.vel[S.nb + i];
+      xs[j][0] = p.x; xs[j][1] = p.y; xs[j][2] = p.z;
+      v[j][0] = u.x; v[j][1] = u.y; v[j][2] = u.z;
+#pragma unroll
+      for (int k = 0; k < 6; ++k) lam[j][k] = A.lam[(size_t)(S.nb + i) * 6 + k];
+      const int kl = min(i / S.seg, S.L - 1);
+      const float2 pp = A.press[S.lb + kl];
+      pR[j] = pp.x; pL[j] = pp.y;
+    } else {
+      xs[j][0] = xs[j][1] = xs[j][2] = 0.f;
+      v[j][0] = v[j][1] = v[j][2] = 0.f;
+#pragma unroll
+      for (int k = 0; k < 6; ++k) lam[j][k] = 0.f;
+      pR[j] = pL[j] = 0.f;
+    }
+  }
+
+  float rmax = 0.f;
+  int itot = 0;
+  for (int st = 0; st < A.n_steps; ++st) {
+    rmax = 0.f;
+    itot = 0;
+    for (int s = 0; s < A.n_sub; ++s) {
+      // (a1) gait target at the end of the substep, (a2) chamber latency, (a3) rest angle
+      const double tp = ((double)(A.step_index + st) * A.n_sub + (double)(s + 1)) * A.h_d;
+      double cyc = (double)P.gait_freq * tp;
+      cyc -= floor(cyc);
+      const float phase = 6.283185307179586f * (float)cyc;
+#pragma unroll
+      for (int j = 0; j < NPL; ++j) {
+        const int i = q * NPL + j;
+        if (!(valid && i < S.N)) continue;
+        const int kl = min(i / S.seg, S.L - 1);
+        float u;
+        if (A.ucmd) {
+          u = A.ucmd[S.lb + kl];
+        } else {
+          float a = P.gait_offset + P.gait_scale * sinf(phase + (float)kl * P.gait_lag);
+          a = fminf(1.f, fmaxf(-1.f, a)) * P.gait_amp;
+          if (P.gait_alternate != 0.f && (kl & 1)) a = -a;
+          u = a;
+        }
+        const float tR = fmaxf(u, 0.f), tL = fmaxf(-u, 0.f);
+        pR[j] = tR + (pR[j] - tR) * (tR > pR[j] ? S.e_inf : S.e_def);
+        pL[j] = tL + (pL[j] - tL) * (tL > pL[j] ? S.e_inf : S.e_def);
+        th[j] = (i % S.seg == 0) ? 0.f : S.gain * (pR[j] - pL[j]) * S.L0;
+      }
+      // (a4) predict: the substep starts at x = xs + dx; dx restarts at h v
+#pragma unroll
+      for (int j = 0; j < NPL; ++j) {
+        const int i = q * NPL + j;
+        xs[j][0] += dx[j][0]; xs[j][1] += dx[j][1]; xs[j][2] += dx[j][2];
+        dx[j][0] = dx[j][1] = dx[j][2] = 0.f;
+        if (valid && i < S.N && i >= S.nfix) {
+          v[j][0] += h * A.g[0]; v[j][1] += h * A.g[1]; v[j][2] += h * A.g[2];
+          dx[j][0] = h * v[j][0]; dx[j][1] = h * v[j][1]; dx[j][2] = h * v[j][2];
+        }
+      }
+      // substep-start positions of the neighbours across the lane boundary
+      float xsl[3], xsr[3];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        xsl[d] = __shfl_up_sync(kFull, xs[NPL - 1][d], 1, G);
+        xsr[d] = __shfl_down_sync(kFull, xs[0][d], 1, G);
+      }
+      // multipliers at the start of the substep
+      bool stop;
+      if (A.warm == 0) {
+#pragma unroll
+        for (int j = 0; j < NPL; ++j)
+#pragma unroll
+          for (int k = 0; k < 6; ++k) lam[j][k] = 0.f;
+      } else {
+        if (A.warm == 2 && A.lam0) {
+#pragma unroll
+          for (int j = 0; j < NPL; ++j) {
+            const int i = q * NPL + j;
+            if (valid && i < S.N)
+#pragma unroll
+              for (int k = 0; k < 6; ++k)
+                lam[j][k] = A.lam0[((size_t)s * A.total_nodes + S.nb + i) * 6 + k];
+          }
+        }
+        row_pass<NPL, G, true>(S, A, q, valid, 0, xs, dx, xsl, xsr, lam, th, stop);
+      }
+      // (a5, a6) Jacobi iterations until the residual reaches tol or the cap
+      bool done = !valid;
+      float rs = 0.f;
+      int ks = 0;
+      for (int k = 0;; ++k) {
+        const float r = row_pass<NPL, G, false>(S, A, q, !done, k, xs, dx, xsl, xsr, lam, th, stop);
+        if (!done && stop) { done = true; rs = r; ks = k; }
+        if (__all_sync(kFull, done)) break;
+      }
+      rmax = fmaxf(rmax, rs);
+      if (!(rs <= 3.0e38f)) rmax = INFINITY;
+      itot += ks;
+      // (a7) velocity from the substep displacement with exponential damping
+#pragma unroll
+      for (int j = 0; j < NPL; ++j) {
+        const int i = q * NPL + j;
+        if (valid && i < S.N && i >= S.nfix) {
+          v[j][0] = dx[j][0] * S.damp_over_h;
+          v[j][1] = dx[j][1] * S.damp_over_h;
+          v[j][2] = dx[j][2] * S.damp_over_h;
+        } else {
+          v[j][0] = v[j][1] = v[j][2] = 0.f;
+        }
+      }
+      if (A.lam_log && valid) {
+        // per-substep converged multipliers (training data of the warm start)
+#pragma unroll
+        for (int j = 0; j < NPL; ++j) {
+          const int i = q * NPL + j;
+          if (i < S.N)
+#pragma unroll
+            for (int k = 0; k < 6; ++k)
+              A.lam_log[((size_t)s * A.total_nodes + S.nb + i) * 6 + k] = lam[j][k];
+        }
+      }
+    }
+  }
+  if (!valid) return;
+#pragma unroll
+  for (int j = 0; j < NPL; ++j) {
+    const int i = q * NPL + j;
+    if (i >= S.N) continue;
+    const float wi = (i < S.nfix) ? 0.f : S.inv_m;
+    A.pos[S.nb + i] = make_float4(xs[j][0] + dx[j][0], xs[j][1] + dx[j][1], xs[j][2] + dx[j][2], wi);
+    A.vel[S.nb + i] = make_float4(v[j][0], v[j][1], v[j][2], 0.f);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) A.lam[(size_t)(S.nb + i) * 6 + k] = lam[j][k];
+    if (i % S.seg == 0 && i / S.seg < S.L) A.press[S.lb + i / S.seg] = make_float2(pR[j], pL[j]);
+  }
+  if (q == 0) {
+    A.resid[snake] = rmax;
+    A.iters[snake] = itot;
+    int st = 0;
+    if (!(rmax <= 3.0e38f)) st = -4;          // SIM_ENAN
+    else if (A.tol > 0.f && rmax > A.tol) st = 1;  // SIM_NOT_CONVERGED
+    A.status[snake] = st;
+  }
+}
+
+}  // namespace snakesim

@@ -1,0 +1,91 @@
+"""The C-ABI library: it loads, exports every entry point include/snakesim.h declares, its
+struct layouts agree with the binding's, and argument validation answers without a GPU."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "snakesim.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1904_02833_gb300.build import build
+    build()
+    from paper_1904_02833_gb300 import _native
+    return _native.load()
+
+
+def declared():
+    src = open(HEADER).read()
+    return sorted(set(re.findall(r"^(?:SimStatus|const char\*)\s+(sim_\w+)\s*\(", src, re.M)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(lib, n), n
+    from paper_1904_02833_gb300 import _native
+    assert set(names) - {"sim_last_error"} <= set(_native.SIGNATURES)
+
+
+def test_struct_layout_matches_header(tmp_path):
+    from paper_1904_02833_gb300 import _native as N
+    c = tmp_path / "sz.c"
+    fields = ["n_links", "n_fixed", "L0", "alpha_b", "gait_amp", "yaw0"]
+    body = "\n".join('printf("%%zu\\n", offsetof(SnakeParams, %s));' % f for f in fields)
+    c.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "snakesim.h"\nint main(void){'
+                 'printf("%zu\\n%zu\\n", sizeof(SimConfig), sizeof(SnakeParams));'
+                 'printf("%zu\\n%zu\\n", offsetof(SimConfig, tol), offsetof(SimConfig, warm));'
+                 + body + "return 0;}\n")
+    exe = tmp_path / "sz"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(c), "-o", str(exe)], check=True)
+    out = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    assert out[0] == ctypes.sizeof(N.SimConfig)
+    assert out[1] == ctypes.sizeof(N.SnakeParams)
+    assert out[2] == N.SimConfig.tol.offset and out[3] == N.SimConfig.warm.offset
+    for f, off in zip(fields, out[4:]):
+        assert getattr(N.SnakeParams, f).offset == off, f
+
+
+def test_argument_validation_without_gpu(lib):
+    """Invalid arguments are rejected before any CUDA call, with a message."""
+    from paper_1904_02833_gb300 import _native as N
+    from paper_1904_02833_gb300.sim import make_config, make_params
+    import workloads as W
+
+    cfg = make_config(W.solver_settings())
+    prm = make_params(W.single_snake())
+    h = ctypes.c_void_p()
+    assert lib.sim_create(ctypes.byref(cfg), 0, prm, None, ctypes.byref(h)) == N.SIM_EINVAL
+    assert h.value is None
+    assert b"n_snakes" in lib.sim_last_error()
+    bad = make_params(W.single_snake())
+    bad[0].mass = 0.0
+    assert lib.sim_create(ctypes.byref(cfg), 1, bad, None, ctypes.byref(h)) == N.SIM_EINVAL
+    long = make_params(W.single_snake())
+    long[0].n_links = 20  # 201 nodes > 128
+    assert lib.sim_create(ctypes.byref(cfg), 1, long, None, ctypes.byref(h)) == N.SIM_EINVAL
+    cfg2 = make_config(W.solver_settings(n_sub=0))
+    assert lib.sim_create(ctypes.byref(cfg2), 1, prm, None, ctypes.byref(h)) == N.SIM_EINVAL
+    assert lib.sim_create(ctypes.byref(cfg), 1, prm, None, None) == N.SIM_EINVAL
+    # calls on a null handle
+    assert lib.sim_step(None, 1) == N.SIM_EINVAL
+    assert lib.sim_set_config(None, ctypes.byref(cfg)) == N.SIM_EINVAL
+    assert lib.sim_get_state(None, None, None, None, None, None, 0) == N.SIM_EINVAL
+    assert lib.sim_autotune(None, 1) == N.SIM_EINVAL
+    assert lib.sim_destroy(None) == N.SIM_OK
+
+
+def test_product_path_has_no_oracle_dependency():
+    """The package never imports or loads the oracle (it is test infrastructure)."""
+    pkg = os.path.join(ROOT, "paper_1904_02833_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                txt = open(os.path.join(dirpath, f)).read()
+                assert "oracle" not in txt.lower(), os.path.join(dirpath, f)

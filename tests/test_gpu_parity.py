@@ -1,0 +1,249 @@
+"""Parity of the CUDA path (through the C-ABI) with the FP64 oracle on the same seeded
+inputs, element by element.
+
+Tolerances (FP32 kernel against FP64 oracle):
+  * positions after one env-step: 1e-5 relative to the largest coordinate;
+  * velocities: v = d / h amplifies the FP32 rounding of the substep displacement d
+    (|d| ~ 1e-4 m, ulp ~ 1e-11 m, 200 Jacobi updates) by 1/h = 1200, and the friction
+    cone projection (a non-smooth branch) passes differences on; bound 2e-4 m/s;
+  * chamber pressures: the filter is an exponential relaxation, FP32 relative rounding
+    per substep accumulates to < 1e-6;
+  * trajectories of 1 s before contact: 1e-3 m; static equilibria: 1e-4 relative.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1904_02833_gb300.build import build
+    build()
+    torch.cuda.set_device(0)
+
+
+def Sim(w, s):
+    from paper_1904_02833_gb300.sim import SnakeSim
+    return SnakeSim(w, s)
+
+
+def ragged_batch():
+    """Every link count 1..8 (11..81 nodes), several of each, in scrambled order."""
+    w = W.batched(n=37, seed=21, links=(1, 8))
+    w["n_links"][:8] = np.arange(1, 9)
+    return w
+
+
+def compare(gpu, ref, pos_rel=1e-5, vel_abs=2e-4):
+    st = gpu.state_host()
+    scale = np.abs(ref.x).max()
+    ep = np.abs(st["pos"] - ref.x).max()
+    ev = np.abs(st["vel"] - ref.v).max()
+    epr = np.abs(st["press"] - ref.press).max()
+    assert ep <= pos_rel * scale, (ep, scale)
+    assert ev <= vel_abs, ev
+    assert epr <= 1e-6, epr
+    return st
+
+
+def test_one_step_single_snake():
+    w = W.single_snake()
+    s = W.solver_settings(iters=10)
+    g, o = Sim(w, s), oracle.OracleSim(w, s)
+    for _ in range(3):
+        g.step(1)
+        o.step(1)
+        st = compare(g, o)
+        assert st["iters"][0] == o.iters[0] == 200
+        assert st["resid"][0] == pytest.approx(o.resid[0], rel=1e-3)
+
+
+@pytest.mark.parametrize("warm", [0, 1])
+def test_one_step_ragged_batch(warm):
+    w = ragged_batch()
+    s = W.solver_settings(iters=10, warm=warm)
+    g, o = Sim(w, s), oracle.OracleSim(w, s)
+    g.step(1)
+    o.step(1)
+    st = compare(g, o)
+    assert np.array_equal(st["iters"], o.iters)
+    lam = g.lam().cpu().numpy()
+    assert np.abs(lam - o.lam).max() <= 1e-3 * np.abs(o.lam).max()
+
+
+def test_every_layout_matches_oracle():
+    """Each admissible lanes x nodes-per-lane layout of each snake length."""
+    w = ragged_batch()
+    s = W.solver_settings(iters=10)
+    o = oracle.OracleSim(w, s)
+    o.step(1)
+    nodes = sorted(set((w["n_links"] * 10 + 1).tolist()))
+    for G in (8, 16, 32):
+        for npl in (1, 2, 3, 4):
+            g = Sim(w, s)
+            used = False
+            for N in nodes:
+                if G * npl >= N:
+                    g.set_layout(N, G, npl)
+                    used = True
+            if not used:
+                continue
+            g.step(1)
+            compare(g, o)
+            g.close()
+
+
+def test_trajectory_before_contact():
+    """One second (60 env-steps) of a gait-driven snake in the air: 1e-3 m."""
+    w = W.subset(W.batched(n=8, seed=5), range(8))
+    w["z0"][:] = 2.0
+    s = W.solver_settings(iters=10, contact=False)
+    g, o = Sim(w, s), oracle.OracleSim(w, s)
+    for _ in range(6):
+        g.step(10)
+        o.step(10)
+    st = g.state_host()
+    assert np.abs(st["pos"] - o.x).max() < 1e-3
+
+
+def test_tolerance_mode_reaches_tol_like_oracle():
+    w = W.subset(ragged_batch(), range(12))
+    s = W.solver_settings(iters=5000, tol=1e-4)
+    g, o = Sim(w, s), oracle.OracleSim(w, s)
+    for _ in range(2):
+        g.step(1)
+        o.step(1)
+    st = g.state_host()
+    worst, per = g.status()
+    assert worst == 0 and (per == 0).all()
+    assert (st["resid"] <= 1e-4).all()
+    rel = np.abs(st["iters"] - o.iters) / o.iters
+    assert rel.max() < 0.05, (st["iters"], o.iters)
+    assert np.abs(st["pos"] - o.x).max() < 1e-4 * np.abs(o.x).max()
+
+
+def test_static_sweep_closed_forms():
+    """256 cantilevers (16 pressures x 16 bend compliances) run to residual 1e-6.
+    Without gravity each settles to the exact discrete arc of its pressure; under gravity
+    at p = 0 the stiffest sag like the discrete Euler-Bernoulli cantilever; every one
+    matches the oracle's equilibrium."""
+    w = W.static_sweep()
+    w["damping"][:] = 20.0
+    # gravity off: arcs
+    s = W.solver_settings(iters=20000, tol=1e-6, gravity=(0, 0, 0), contact=False)
+    g = Sim(w, s)
+    press = np.stack([w["gait_offset"], np.zeros(256)], 1).astype(np.float32)
+    g.set_state(press=press)
+    g.step(150)
+    st = g.state_host()
+    assert (st["resid"] <= 1e-6).all()
+    L0 = 0.02
+    for k in range(256):
+        p = w["gait_offset"][k]
+        th = 20.0 * p * L0
+        head, ref = 0.0, [np.array([0.0, 0, 1.0]), np.array([L0, 0, 1.0])]
+        for i in range(1, 10):
+            head += th
+            ref.append(ref[-1] + L0 * np.array([math.cos(head), math.sin(head), 0]))
+        x = st["pos"][11 * k:11 * k + 11]
+        assert np.abs(x - np.array(ref)).max() < 1e-4 * 0.2, k
+    # gravity on, pressure on: against the oracle; p = 0 stiff ones against the closed form
+    s = W.solver_settings(iters=20000, tol=1e-6, contact=False)
+    g = Sim(w, s)
+    g.set_state(press=press)
+    g.step(150)
+    st = g.state_host()
+    assert (st["resid"] <= 1e-6).all()
+    sel = list(range(0, 256, 17)) + [1, 2, 3]
+    o = oracle.OracleSim(W.subset(w, sel), s)
+    o.press[:, 0] = w["gait_offset"][sel]
+    o.step(150)
+    for j, k in enumerate(sel):
+        xg = st["pos"][11 * k:11 * k + 11]
+        xo = o.x[11 * j:11 * j + 11]
+        assert np.abs(xg - xo).max() < 1e-4 * np.abs(xo - xo[0]).max() + 1e-7, k
+    m, G = 0.01, 9.81
+    for k in range(16):  # pressure level 0
+        ab = w["alpha_b"][k]
+        sag = sum(ab * m * G * sum((j - i) * L0 for j in range(i + 1, 11)) / L0 ** 2 * (10 - i) * L0
+                  for i in range(1, 10))
+        drop = st["pos"][11 * k, 2] - st["pos"][11 * k + 10, 2]
+        if sag < 2e-3:  # small-deflection regime
+            assert drop == pytest.approx(sag, rel=2e-2), (k, ab)
+
+
+def test_command_override_matches_oracle():
+    w = W.subset(ragged_batch(), range(6))
+    s = W.solver_settings(iters=10)
+    g, o = Sim(w, s), oracle.OracleSim(w, s)
+    u = np.linspace(-1, 1, g.n_links)
+    g.set_pressure(torch.tensor(u, dtype=torch.float32))
+    g.step(2)
+    o.step(2, ucmd=u)
+    compare(g, o)
+    g.set_pressure(None)
+    g.step(1)
+    o.step(1)
+    compare(g, o)
+
+
+def test_graph_replay_is_bitwise_identical_to_direct_launch():
+    w = ragged_batch()
+    s = W.solver_settings(iters=10)
+    a, b = Sim(w, s), Sim(w, s)
+    for _ in range(3):
+        a.step(2)
+        b.step(2, graph=True)
+    sa, sb = a.state_host(), b.state_host()
+    for k in ("pos", "vel", "press", "resid", "iters"):
+        assert np.array_equal(sa[k], sb[k]), k
+
+
+def test_state_roundtrip_zero_steps_and_nan_status():
+    w = ragged_batch()
+    s = W.solver_settings(iters=10)
+    g = Sim(w, s)
+    g.step(1)
+    st = g.state_host()
+    lam = g.lam()
+    h = Sim(w, s)
+    h.set_state(pos=st["pos"], vel=st["vel"], press=st["press"], lam=lam)
+    h.step_index = g.step_index
+    h.step(0)
+    st2 = h.state_host()
+    assert np.array_equal(st2["pos"], st["pos"]) and np.array_equal(st2["vel"], st["vel"])
+    g.step(1)
+    h.step(1)
+    assert np.array_equal(g.state_host()["pos"], h.state_host()["pos"])
+    # a non-finite node is reported for its snake only
+    pos = st["pos"].copy()
+    pos[int(h.node_off[3]) + 2, 0] = np.nan
+    h.set_state(pos=pos)
+    h.step(1)
+    worst, per = h.status()
+    assert worst == -4 and per[3] == -4 and (np.delete(per, 3) == 0).all()
+
+
+def test_full_size_sampled_parity():
+    """4096 uneven snakes in the benchmark's launch configuration; 16 sampled snakes
+    recomputed by the oracle alone (snakes are independent)."""
+    w = W.batched(n=4096)
+    s = W.solver_settings(iters=10)
+    g = Sim(w, s)
+    g.step(2)
+    st = g.state_host()
+    rng = np.random.default_rng(0)
+    sel = np.sort(rng.choice(4096, 16, replace=False))
+    o = oracle.OracleSim(W.subset(w, sel), s)
+    o.step(2)
+    for j, k in enumerate(sel):
+        xg = st["pos"][g.node_off[k]:g.node_off[k + 1]]
+        xo = o.x[o.node_off[j]:o.node_off[j + 1]]
+        assert np.abs(xg - xo).max() <= 1e-5 * np.abs(xo).max(), k
