@@ -135,12 +135,16 @@ def run_gpu(args):
     for _ in range(args.warmup):
         sim.step(1, graph=True)
     barrier()
+    start_state = sim.state()
+    start_lam = sim.lam()
+    start_index = sim.step_index
     l0 = sim.launches()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
     node_iters = 0
     resid_max = 0.0
     unconverged = 0
+    it_max, it_mean = [], []
     with Clocks(local) as clk:
         barrier()
         for k in range(args.steps):
@@ -151,8 +155,10 @@ def run_gpu(args):
             st = sim.state()
             # Jacobi passes: the applied updates plus the one evaluation per substep that
             # finds the residual below tol (or the cap) and stops
-            passes_snake = st["iters"].double().cpu().numpy() + s["n_sub"]
-            node_iters += int((passes_snake * n_nodes_snake).sum())
+            its = st["iters"].double().cpu().numpy()
+            node_iters += int(((its + s["n_sub"]) * n_nodes_snake).sum())
+            it_max.append(float(its.max()) / s["n_sub"])
+            it_mean.append(float(its.mean()) / s["n_sub"])
             resid_max = max(resid_max, float(st["resid"].max()))
             unconverged += int((st["resid"] > TOL).sum())
         barrier()
@@ -166,29 +172,32 @@ def run_gpu(args):
     env_steps = N_SNAKES * args.steps * world
     value = env_steps / t
 
-    # end to end through the public API with host buffers (pinned), copies inside the timing
-    st0 = sim.state_host()
-    hp = torch.from_numpy(st0["pos"]).pin_memory()
-    hv = torch.from_numpy(st0["vel"]).pin_memory()
-    hpr = torch.from_numpy(st0["press"]).pin_memory()
-    out = {k: torch.empty(v.shape, dtype=torch.from_numpy(v).dtype).pin_memory() for k, v in st0.items()}
-    e2e_steps = max(2, min(args.steps, 5))
+    # End to end through the public API with the state in pinned host memory: the same
+    # K env-steps again from the same start, every step copying the state in, stepping
+    # and copying the new state, residuals and update counts out.
+    sim.set_state(pos=start_state["pos"], vel=start_state["vel"], press=start_state["press"],
+                  lam=start_lam)
+    sim.step_index = start_index
+    host = {k: v.cpu().pin_memory() for k, v in sim.state().items()}
+    host["lam"] = start_lam.cpu().pin_memory()
+    inputs = ("pos", "vel", "press", "lam")
     barrier()
     t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        sim.set_state(pos=hp.cuda(non_blocking=True), vel=hv.cuda(non_blocking=True),
-                      press=hpr.cuda(non_blocking=True))
+    for _ in range(args.steps):
+        dev = {k: host[k].to("cuda", non_blocking=True) for k in inputs}
+        sim.set_state(pos=dev["pos"], vel=dev["vel"], press=dev["press"], lam=dev["lam"])
         sim.step(1, graph=True)
         d = sim.state()
-        for k in out:
-            out[k].copy_(d[k], non_blocking=True)
+        d["lam"] = sim.lam()
+        for k in host:
+            host[k].copy_(d[k], non_blocking=True)
     torch.cuda.synchronize()
     t_e2e = time.perf_counter() - t0
     te = torch.tensor([t_e2e], dtype=torch.float64, device="cuda")
     if world > 1:
         dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    h2d = int(hp.numel() * 4 + hv.numel() * 4 + hpr.numel() * 4)
-    d2h = int(sum(v.numel() * v.element_size() for v in out.values()))
+    h2d = int(sum(host[k].numel() * host[k].element_size() for k in inputs))
+    d2h = int(sum(v.numel() * v.element_size() for v in host.values()))
 
     if rank == 0:
         pk = peaks()
@@ -222,7 +231,9 @@ def run_gpu(args):
                        "warm_start": "cold", "l2": "flushed between timed steps (256 MB write)",
                        "parallelism": "independent snakes per GPU (dp%d)" % world},
             "residual": {"max": resid_max, "unconverged_snake_steps": unconverged,
-                         "mean_passes_per_substep": node_iters / total_nodes / args.steps / 20},
+                         "mean_passes_per_substep": node_iters / total_nodes / args.steps / 20,
+                         "updates_per_substep_mean_by_step": it_mean,
+                         "updates_per_substep_max_by_step": it_max},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
                          "frac": achieved / alu_peak, "traffic": None,
                          "kernel": "snake_solver_kernel<NPL> (one per nodes-per-lane, concurrent)",
@@ -232,7 +243,7 @@ def run_gpu(args):
                                  "peak_gbs": pk.get("hbm_gbs"),
                                  "frac": bytes_step / (t_local / args.steps) / 1e9 / pk["hbm_gbs"]
                                  if pk.get("hbm_gbs") else None}},
-            "e2e": {"value": N_SNAKES * e2e_steps * world / float(te.item()), "unit": "env-steps/s",
+            "e2e": {"value": N_SNAKES * args.steps * world / float(te.item()), "unit": "env-steps/s",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": int(launches),
             "clocks": clocks,
@@ -311,9 +322,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--snakes", type=int, default=N_SNAKES,
+                    help="batch size per GPU (smaller batches for profiler captures)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    global N_SNAKES
+    N_SNAKES = args.snakes
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -43,8 +43,11 @@ SimStatus fail(SimStatus s, const std::string& msg) {
 // ------------------------------------------------------------------ kernels
 // One kernel per nodes-per-lane count (each gets the register budget of its own layout);
 // the host launches the ones that have work on forked streams so that they run together.
+#ifndef SNAKE_MIN_BLOCKS
+#define SNAKE_MIN_BLOCKS 1
+#endif
 template <int NPL>
-__global__ void __launch_bounds__(128) snake_solver_kernel(SolverArgs A) {
+__global__ void __launch_bounds__(128, SNAKE_MIN_BLOCKS) snake_solver_kernel(SolverArgs A) {
   const int warp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
   const int lane = threadIdx.x & 31;

@@ -74,7 +74,7 @@ __device__ __forceinline__ float group_max(float r) {
 // Per-group constants of one snake.
 struct SnakeK {
   int N, seg, nfix, L, nb, lb;
-  float L0, inv_m, at_s, at_b, mu, radius, gain, e_inf, e_def, damp_over_h;
+  float L0, inv_L0, inv_m, mass, at_s, at_b, mu, radius, gain, e_inf, e_def, damp_over_h;
 };
 
 // One pass over the rows at the current positions and multipliers.
@@ -149,7 +149,7 @@ __device__ __forceinline__ float row_pass(const SnakeK& S, const SolverArgs& A, 
         float d;
         if (WARM) d = lam[j][0];
         else {
-          r = fmaxf(r, fabsf(c + S.at_s * l) / L0);
+          r = fmaxf(r, fabsf(c + S.at_s * l) * S.inv_L0);
           d = A.omega * (-c - S.at_s * l) / (wg + S.at_s);
         }
         dl[j][0] = d;
@@ -174,7 +174,7 @@ __device__ __forceinline__ float row_pass(const SnakeK& S, const SolverArgs& A, 
           if (WARM) d = lam[j][1];
           else {
             const float l = lam[j][1];
-            r = fmaxf(r, fabsf(c + S.at_b * l) / L0);
+            r = fmaxf(r, fabsf(c + S.at_b * l) * S.inv_L0);
             d = A.omega * (-c - S.at_b * l) / (wg + S.at_b);
           }
           dl[j][1] = d;
@@ -197,7 +197,7 @@ __device__ __forceinline__ float row_pass(const SnakeK& S, const SolverArgs& A, 
           if (WARM) d = lam[j][2];
           else {
             const float l = lam[j][2];
-            r = fmaxf(r, fabsf(c + S.at_b * l) / L0);
+            r = fmaxf(r, fabsf(c + S.at_b * l) * S.inv_L0);
             d = A.omega * (-c - S.at_b * l) / (wg + S.at_b);
           }
           dl[j][2] = d;
@@ -217,7 +217,7 @@ __device__ __forceinline__ float row_pass(const SnakeK& S, const SolverArgs& A, 
       else {
         // residuals: Fischer-Burmeister on (c_n, w lambda_n); natural map of the disc
         const float b = wi * ln;
-        r = fmaxf(r, fabsf(cn + b - sqrtf(cn * cn + b * b)) / L0);
+        r = fmaxf(r, fabsf(cn + b - sqrtf(cn * cn + b * b)) * S.inv_L0);
         const float rho = wi * S.mu * ln;
         const float ax = wi * lam[j][4], ay = wi * lam[j][5];
         float px = ax - ux, py = ay - uy;
@@ -225,14 +225,14 @@ __device__ __forceinline__ float row_pass(const SnakeK& S, const SolverArgs& A, 
         if (pn > rho) {
           if (rho > 0.f) { px *= rho / pn; py *= rho / pn; } else { px = 0.f; py = 0.f; }
         }
-        r = fmaxf(r, sqrtf((ax - px) * (ax - px) + (ay - py) * (ay - py)) / L0);
+        r = fmaxf(r, sqrtf((ax - px) * (ax - px) + (ay - py) * (ay - py)) * S.inv_L0);
         // contact: lambda_n <- max(0, lambda_n + omega (-c_n / w))
-        const float nl = fmaxf(0.f, ln + A.omega * (-cn / wi));
+        const float nl = fmaxf(0.f, ln - A.omega * cn * S.mass);
         dn = nl - ln;
         // friction: relaxed update projected onto |lambda_t| <= mu lambda_n (current
         // iterate's lambda_n)
-        float tx = lam[j][4] + A.omega * (-ux / wi);
-        float ty = lam[j][5] + A.omega * (-uy / wi);
+        float tx = lam[j][4] - A.omega * ux * S.mass;
+        float ty = lam[j][5] - A.omega * uy * S.mass;
         const float rad = S.mu * ln;
         const float n2 = tx * tx + ty * ty;
         if (n2 > rad * rad) {
@@ -294,7 +294,7 @@ __device__ void run_group(const SolverArgs& A, int snake, bool valid) {
   S.seg = P.seg_per_link; S.nfix = P.n_fixed; S.L = P.n_links;
   S.nb = valid ? A.node_off[snake] : 0;
   S.lb = valid ? A.link_off[snake] : 0;
-  S.L0 = P.L0; S.inv_m = 1.0f / P.mass;
+  S.L0 = P.L0; S.inv_L0 = 1.0f / P.L0; S.inv_m = 1.0f / P.mass; S.mass = P.mass;
   S.at_s = P.alpha_s / (h * h); S.at_b = P.alpha_b / (h * h);
   S.mu = P.mu; S.radius = P.radius; S.gain = P.gain;
   S.e_inf = expf(-h / P.tau_inf); S.e_def = expf(-h / P.tau_def);
@@ -403,8 +403,14 @@ __device__ void run_group(const SolverArgs& A, int snake, bool valid) {
         if (!done && stop) { done = true; rs = r; ks = k; }
         if (__all_sync(kFull, done)) break;
       }
+      // a non-finite displacement anywhere in the snake marks the step (fmaxf drops NaN)
+      float bad = 0.f;
+#pragma unroll
+      for (int j = 0; j < NPL; ++j)
+        if (!(fabsf(dx[j][0]) + fabsf(dx[j][1]) + fabsf(dx[j][2]) <= 3.0e38f)) bad = 1.f;
+      bad = group_max<G>(bad);
       rmax = fmaxf(rmax, rs);
-      if (!(rs <= 3.0e38f)) rmax = INFINITY;
+      if (!(rs <= 3.0e38f) || bad > 0.f) rmax = INFINITY;
       itot += ks;
       // (a7) velocity from the substep displacement with exponential damping
 #pragma unroll
