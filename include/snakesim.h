@@ -70,7 +70,9 @@ typedef struct {
   float gravity[3];   /* [m/s^2]                                                         */
   int32_t contact;    /* 1: ground plane z = 0 with Coulomb friction                     */
   int32_t warm;       /* SIM_WARM_*                                                      */
-  int32_t reserved;
+  float beta;         /* weight of the previous substep's multipliers in a warm start:   *
+                       * PREVIOUS starts from beta lambda_prev, LEARNED from              *
+                       * beta lambda_prev + m g h^2 y (y: the network's output)          */
 } SimConfig;
 
 /* Per-snake parameters (host layout, 96 bytes). */
@@ -174,11 +176,68 @@ SimStatus sim_set_layout(SimHandle* h, int nodes, int lanes, int nodes_per_lane)
  * afterwards (the graph is rebuilt when the configuration or layout changes). */
 SimStatus sim_step_graph(SimHandle* h, int n_steps);
 
+/* Saves / restores the whole simulation state (positions, velocities, pressures,
+ * multipliers, env-step counter, substep position of split stepping) in a
+ * library-owned snapshot; stream-ordered.  Restoring without a saved snapshot is
+ * SIM_EINVAL. */
+SimStatus sim_snapshot_save(SimHandle* h);
+SimStatus sim_snapshot_restore(SimHandle* h);
+
 /* Kernel launches made by this handle so far (the count the benchmark reports). */
 SimStatus sim_launch_count(SimHandle* h, int64_t* launches);
 
 /* Frees the handle and its device buffers (synchronises the stream).  NULL is ok. */
 SimStatus sim_destroy(SimHandle* h);
+
+/* ---------------------------------------------------------------- learned warm start
+ * A small network predicts the multipliers each substep starts from, so that fewer
+ * Jacobi updates reach the tolerance (no counterpart in the paper, which solves every
+ * step with Newton + PCR from scratch, Sec. IV-D).  Per constraint row it reads 24
+ * features (row kind, the row's node positions and velocities in the row's frame, the
+ * rest angle, the previous substep's multiplier; written by the solver, bf16, padded to
+ * 32 per row) and computes lambda0 / (m g h^2) = w3 . silu(W2 silu(W1 f + b1) + b2) + b3
+ * with hidden width 128, BF16 operands and FP32 accumulation on the tensor cores.
+ * Parameter vector (FP32, MLP_NUM_PARAMS): W1 [128][24], b1 [128], W2 [128][128],
+ * b2 [128], w3 [128], b3. */
+#define MLP_NUM_PARAMS 19841
+typedef struct MlpHandle MlpHandle;
+
+/* Creates a network with all parameters zero, bound to `stream` (cudaStream_t). */
+SimStatus mlp_create(void* stream, MlpHandle** out);
+/* Sets / reads the FP32 parameter vector; setting also resets the Adam moments. */
+SimStatus mlp_set_params(MlpHandle* m, const float* params, int is_device);
+SimStatus mlp_get_params(MlpHandle* m, float* params, int is_device);
+/* out[r] for feat [rows][32] bf16 (device pointers).  Synchronises the stream;
+ * SIM_ECUDA if a tensor-core wait timed out. */
+SimStatus mlp_forward(MlpHandle* m, const void* feat, int64_t rows, float* out);
+/* Gradient of L = scale * sum_r (y_r - target_r)^2 into grad[MLP_NUM_PARAMS] and L into
+ * *loss (device pointers, either may be NULL).  Synchronises the stream. */
+SimStatus mlp_grad(MlpHandle* m, const void* feat, const float* target, int64_t rows,
+                   float scale, float* grad, float* loss);
+/* One Adam step (beta 0.9 / 0.999, eps 1e-8) on the mean squared error over the rows;
+ * *loss (device, may be NULL) receives the loss before the step.  Asynchronous. */
+SimStatus mlp_train_step(MlpHandle* m, const void* feat, const float* target, int64_t rows,
+                         float lr, float* loss);
+/* Synchronises and reports a timed-out tensor-core wait of earlier asynchronous calls. */
+SimStatus mlp_check(MlpHandle* m);
+SimStatus mlp_destroy(MlpHandle* m);
+
+/* Attaches a network to a simulator (NULL detaches).  With warm = SIM_WARM_LEARNED every
+ * substep starts from the network's multipliers; sim_step then runs each substep as
+ * solver launch -> network -> solver launch (captured together by sim_step_graph).
+ * The network must outlive its use by the simulator. */
+SimStatus sim_set_mlp(SimHandle* h, MlpHandle* m);
+
+/* Substep-by-substep stepping (used to log training data).  sim_split_begin starts the
+ * next env-step: it runs the gait, latency filter and prediction of substep 0 and writes
+ * the features of every row.  sim_split_finish completes the current substep (warm start
+ * per the configuration, iterations, velocities) and begins the next one, writing its
+ * features; after the last substep the env-step counter advances.  Rows are
+ * 6 * total_nodes (six slots per node). */
+SimStatus sim_split_begin(SimHandle* h);
+SimStatus sim_split_finish(SimHandle* h);
+/* Device pointer of the feature buffer [rows][32] bf16 and the row count. */
+SimStatus sim_features(SimHandle* h, void** feat, int64_t* rows);
 
 /* Text of the last error raised on the calling thread ("" if none). */
 const char* sim_last_error(void);

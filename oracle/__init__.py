@@ -52,6 +52,9 @@ def lib():
         L.oracle_rows.argtypes = [ctypes.c_int, ctypes.c_int, P, P, P, P, P, P, P, P]
         L.oracle_calib_grad.argtypes = [ctypes.c_int, P, P, P, P, P, ctypes.c_longlong,
                                         ctypes.c_int, P, P, P, P, P, P, P, ctypes.c_int]
+        L.oracle_features.argtypes = [ctypes.c_int, P, P, P, P, P, ctypes.c_longlong, P, P, P, P,
+                                      P, P]
+        L.oracle_mlp_forward.argtypes = [P, ctypes.c_longlong, P, P]
         assert L.oracle_nprm() == len(PRM_FIELDS)
         _lib = L
     return _lib
@@ -68,7 +71,7 @@ def pack_params(w: dict) -> np.ndarray:
 def pack_cfg(s: dict) -> np.ndarray:
     g = s["gravity"]
     return np.array([s["dt"], s["n_sub"], s["iters"], s["tol"], s["omega"], g[0], g[1], g[2],
-                     1.0 if s["contact"] else 0.0, s["warm"]], np.float64)
+                     1.0 if s["contact"] else 0.0, s["warm"], s.get("beta", 1.0)], np.float64)
 
 
 class OracleSim:
@@ -103,16 +106,26 @@ class OracleSim:
         self.s.update(kw)
         self.cfg = pack_cfg(self.s)
 
-    def step(self, n_steps: int = 1, ucmd=None, tip=False, lam0=None):
+    def step(self, n_steps: int = 1, ucmd=None, tip=False, mlp=None):
+        """mlp: network parameters (used when the settings' warm = 2)."""
         u = None if ucmd is None else np.ascontiguousarray(ucmd, np.float64)
         tips = np.zeros((n_steps, self.n, 3)) if tip else None
-        l0 = None if lam0 is None else np.ascontiguousarray(lam0, np.float64)
+        l0 = None if mlp is None else np.ascontiguousarray(mlp, np.float64)
         lib().oracle_step(self.n, _p(self.nl), _p(self.seg), _p(self.nfix), _p(self.prm),
                           _p(self.cfg), self.step_index, n_steps, _p(self.x), _p(self.v),
                           _p(self.press), _p(self.lam), _p(u), _p(self.resid), _p(self.iters),
                           _p(tips), _p(l0), self.n_threads)
         self.step_index += n_steps
         return tips
+
+    def features(self, ucmd=None):
+        """Features [nodes * 6, 24] of substep 0 of the next env-step (state unchanged)."""
+        u = None if ucmd is None else np.ascontiguousarray(ucmd, np.float64)
+        F = np.zeros((self.n_nodes * NK, 24))
+        lib().oracle_features(self.n, _p(self.nl), _p(self.seg), _p(self.nfix), _p(self.prm),
+                              _p(self.cfg), self.step_index, _p(self.x), _p(self.v), _p(self.press),
+                              _p(self.lam), _p(u), _p(F))
+        return F
 
     def snake_nodes(self, s: int) -> slice:
         return slice(int(self.node_off[s]), int(self.node_off[s + 1]))
@@ -131,6 +144,15 @@ class OracleSim:
                                 _p(self.press), _p(self.lam), _p(tg), _p(loss), _p(grad),
                                 self.n_threads)
         return loss, grad
+
+
+def mlp_forward(params, feat):
+    """Network outputs for features [rows, 24] (bfloat16 operands, FP64 arithmetic)."""
+    p = np.ascontiguousarray(params, np.float64)
+    f = np.ascontiguousarray(feat, np.float64)
+    y = np.zeros(len(f))
+    lib().oracle_mlp_forward(_p(p), len(f), _p(f), _p(y))
+    return y
 
 
 def rows(w1: dict, settings: dict, x, xs, press):

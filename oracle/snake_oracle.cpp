@@ -100,7 +100,7 @@ template <class T> inline T dot(const V3<T>& a, const V3<T>& b) { return a.x * b
 enum { P_L0, P_MASS, P_ALPHA_S, P_ALPHA_B, P_GAIN, P_TAU_INF, P_TAU_DEF, P_MU, P_DAMP,
        P_RADIUS, P_AMP, P_FREQ, P_LAG, P_OFFSET, P_SCALE, P_ALT, P_X0, P_Y0, P_Z0, P_YAW0,
        NPRM };
-enum { C_DT, C_NSUB, C_ITERS, C_TOL, C_OMEGA, C_GX, C_GY, C_GZ, C_CONTACT, C_WARM, NCFG };
+enum { C_DT, C_NSUB, C_ITERS, C_TOL, C_OMEGA, C_GX, C_GY, C_GZ, C_CONTACT, C_WARM, C_BETA, NCFG };
 // Row kinds; a node i owns one multiplier slot per kind: stretch (i, i+1), yaw and
 // pitch bend centred on i, contact of i, friction of i along world x and y.
 enum { R_STRETCH, R_YAW, R_PITCH, R_CONTACT, R_FX, R_FY, NK };
@@ -127,14 +127,14 @@ Snake<T> load_snake(const int* nl, const int* seg, const int* nfix, const double
 }
 
 struct Cfg {
-  double dt, h, tol, omega, g[3];
+  double dt, h, tol, omega, g[3], beta;
   int n_sub, iters, contact, warm;
 };
 Cfg load_cfg(const double* c) {
   Cfg C;
   C.dt = c[C_DT]; C.n_sub = (int)c[C_NSUB]; C.h = C.dt / C.n_sub; C.iters = (int)c[C_ITERS];
   C.tol = c[C_TOL]; C.omega = c[C_OMEGA]; C.g[0] = c[C_GX]; C.g[1] = c[C_GY]; C.g[2] = c[C_GZ];
-  C.contact = (int)c[C_CONTACT]; C.warm = (int)c[C_WARM];
+  C.contact = (int)c[C_CONTACT]; C.warm = (int)c[C_WARM]; C.beta = c[C_BETA];
   return C;
 }
 
@@ -348,13 +348,119 @@ void apply_rows(int N, Rows<T>& R, const std::vector<double>& w, const std::vect
   }
 }
 
+// ---------------------------------------------------------------- warm-start network
+// The learned warm start reads 24 features per constraint row at the predicted positions
+// of a substep and predicts the row's multiplier over m g h^2.  Row frame: horizontal
+// unit tangent t (stretch: the row's segment; bend: the segment into node i; contact:
+// the segment out of node i, the one into it at the last node; friction x / y: world
+// x / y), b = z x t, z.  Features: one-hot row kind (6); height of the row's first node
+// above its contact height, / L0 (1); second and third node relative to the first, in
+// the frame, / L0 (6); velocities of the nodes in the frame, times h / L0 (9); rest angle
+// of a yaw row (1); the row's multiplier of the previous substep / (m g h^2) (1).
+constexpr int kFeat = 24, kHid = 128;
+constexpr int kMlpParams = kHid * kFeat + kHid + kHid * kHid + kHid + kHid + 1;
+
+// Round to the nearest bfloat16 (ties to even), the operand precision of the network.
+double bf16r(double a) {
+  float f = (float)a;
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  if ((u & 0x7f800000u) != 0x7f800000u) u += 0x7fffu + ((u >> 16) & 1u);
+  u &= 0xffff0000u;
+  std::memcpy(&f, &u, 4);
+  return (double)f;
+}
+
+double silu_exact(double z) { return z / (1.0 + std::exp(-z)); }
+
+// One forward pass: operands (features, W1, W2, first hidden layer) rounded to bfloat16
+// as the tensor cores read them, everything else in FP64.
+double mlp_forward(const double* P, const double* f) {
+  const double* W1 = P;
+  const double* b1 = W1 + kHid * kFeat;
+  const double* W2 = b1 + kHid;
+  const double* b2 = W2 + kHid * kHid;
+  const double* w3 = b2 + kHid;
+  const double b3 = w3[kHid];
+  double h1[kHid];
+  for (int o = 0; o < kHid; ++o) {
+    double z = b1[o];
+    for (int i = 0; i < kFeat; ++i) z += bf16r(W1[o * kFeat + i]) * bf16r(f[i]);
+    h1[o] = bf16r(silu_exact(z));
+  }
+  double y = b3;
+  for (int o = 0; o < kHid; ++o) {
+    double z = b2[o];
+    for (int i = 0; i < kHid; ++i) z += bf16r(W2[o * kHid + i]) * h1[i];
+    y += w3[o] * silu_exact(z);
+  }
+  return y;
+}
+
+// Features of every row of one snake ([N][6][24]) at positions X, velocities v,
+// previous multipliers lam and rest angles theta.
+template <class T>
+void row_features(const Snake<T>& S, const Cfg& C, const std::vector<V3<T>>& X, const V3<T>* v,
+                  const std::vector<T>& lam, const std::vector<T>& theta, double* F) {
+  const int N = S.N;
+  const double L0 = val(S.L0), h = C.h;
+  const double lsc = 1.0 / (val(S.mass) * 9.81 * h * h);
+  auto P = [&](int i) { return V3<double>{val(X[i].x), val(X[i].y), val(X[i].z)}; };
+  auto dirh = [&](int b, int a, double& tx, double& ty) {
+    double ex = val(X[b].x) - val(X[a].x), ey = val(X[b].y) - val(X[a].y);
+    double n = std::sqrt(ex * ex + ey * ey);
+    if (n > 0.0) { tx = ex / n; ty = ey / n; } else { tx = 1.0; ty = 0.0; }
+  };
+  for (int i = 0; i < N; ++i) {
+    for (int k = 0; k < NK; ++k) {
+      double* f = F + ((size_t)i * NK + k) * kFeat;
+      for (int c = 0; c < kFeat; ++c) f[c] = 0.0;
+      bool ex = (k == R_STRETCH) ? (i <= N - 2)
+              : (k == R_YAW || k == R_PITCH) ? (i >= 1 && i <= N - 2)
+              : (C.contact && i >= S.nfix);
+      if (!ex) continue;
+      f[k] = 1.0;
+      int a, b = -1, c = -1;
+      double tx, ty;
+      if (k == R_STRETCH) { a = i; b = i + 1; dirh(i + 1, i, tx, ty); }
+      else if (k == R_YAW || k == R_PITCH) { a = i - 1; b = i; c = i + 1; dirh(i, i - 1, tx, ty); }
+      else {
+        a = i;
+        if (k == R_CONTACT) { if (i + 1 <= N - 1) dirh(i + 1, i, tx, ty); else dirh(i, i - 1, tx, ty); }
+        else if (k == R_FX) { tx = 1.0; ty = 0.0; }
+        else { tx = 0.0; ty = 1.0; }
+      }
+      V3<double> pa = P(a);
+      f[6] = (pa.z - val(S.radius)) / L0;
+      int nodes[3] = {a, b, c};
+      for (int u = 1; u < 3; ++u) {
+        if (nodes[u] < 0) continue;
+        V3<double> d = sub(P(nodes[u]), pa);
+        f[7 + 3 * (u - 1)] = (d.x * tx + d.y * ty) / L0;
+        f[8 + 3 * (u - 1)] = (-d.x * ty + d.y * tx) / L0;
+        f[9 + 3 * (u - 1)] = d.z / L0;
+      }
+      for (int u = 0; u < 3; ++u) {
+        if (nodes[u] < 0) continue;
+        const V3<T>& vv = v[nodes[u]];
+        f[13 + 3 * u] = (val(vv.x) * tx + val(vv.y) * ty) * h / L0;
+        f[14 + 3 * u] = (-val(vv.x) * ty + val(vv.y) * tx) * h / L0;
+        f[15 + 3 * u] = val(vv.z) * h / L0;
+      }
+      if (k == R_YAW) f[22] = val(theta[i]);
+      f[23] = val(lam[i * NK + k]) * lsc;
+    }
+  }
+}
+
 // ---------------------------------------------------------------- one env-step
 // Advances one snake by one env-step of n_sub substeps.  Returns the max residual over
 // the substeps and adds the number of Jacobi updates to *iters.
 template <class T>
 double snake_step(const Snake<T>& S, const Cfg& C, long long step_index, V3<T>* x,
                   V3<T>* v, T* press, T* lam_io, const double* ucmd, int* iters,
-                  const double* lam0_all /* [n_sub][N*NK] or null */) {
+                  const double* mlp /* network parameters for warm = 2, or null */,
+                  double* feat0 = nullptr /* if set: features of substep 0, then return */) {
   const int N = S.N;
   const double h = C.h;
   std::vector<double> w(N);
@@ -394,11 +500,22 @@ double snake_step(const Snake<T>& S, const Cfg& C, long long step_index, V3<T>* 
         X[i].x = X[i].x + h * v[i].x; X[i].y = X[i].y + h * v[i].y; X[i].z = X[i].z + h * v[i].z;
       }
     }
-    // multipliers: cold (0), previous substep's values, or a given warm start.  A
-    // non-zero start also moves the nodes by M^-1 J^T lambda0 (gradients at the predicted
-    // positions), so that M (x - x~) = J^T lambda holds from the first iterate on.
+    if (feat0) { row_features(S, C, X, v, lam, theta, feat0); return 0.0; }
+    // multipliers: cold (0), beta x the previous substep's values, plus the network's
+    // prediction in the learned mode.  A non-zero start also moves the nodes by
+    // M^-1 J^T lambda0 (gradients at the predicted positions), so that
+    // M (x - x~) = J^T lambda holds from the first iterate on.
     if (C.warm == 0) for (auto& l : lam) l = T(0.0);
-    else if (C.warm == 2 && lam0_all) for (size_t j = 0; j < lam.size(); ++j) lam[j] = lam0_all[(size_t)s * N * NK + j];
+    else {
+      std::vector<double> y(lam.size(), 0.0);
+      if (C.warm == 2 && mlp) {
+        std::vector<double> F((size_t)N * NK * kFeat);
+        row_features(S, C, X, v, lam, theta, F.data());
+        for (size_t j = 0; j < lam.size(); ++j) y[j] = mlp_forward(mlp, &F[j * kFeat]);
+      }
+      const double sc = val(S.mass) * 9.81 * h * h;
+      for (size_t j = 0; j < lam.size(); ++j) lam[j] = C.beta * lam[j] + T(y[j] * sc);
+    }
     if (C.warm != 0) {
       eval_rows(S, C, X, XS, theta, R);
       for (int i = 0; i < N; ++i)
@@ -478,6 +595,7 @@ Offsets offsets(int n, const int* nl, const int* seg) {
 extern "C" {
 
 int oracle_nprm() { return NPRM; }
+int oracle_mlp_params() { return kMlpParams; }
 int oracle_ncfg() { return NCFG; }
 
 // Straight initial pose along the heading yaw0 from (x0, y0, z0), at rest, chambers
@@ -503,11 +621,11 @@ int oracle_init(int n, const int* nl, const int* seg, const double* prm, double*
 // lam: [nodes][6]; ucmd: optional [links] command held for these steps (null = gait);
 // resid/iters: per snake, max residual and total updates of the last step;
 // tip: optional [n_steps][n][3] last-node positions after each step;
-// lam0: optional learned warm start, [n_sub][nodes][6] for a single step (n_steps = 1).
+// mlp: network parameters (19841 doubles) used when the configuration's warm = 2.
 int oracle_step(int n, const int* nl, const int* seg, const int* nfix, const double* prm,
                 const double* cfg, long long step_index, int n_steps, double* x, double* v,
                 double* press, double* lam, const double* ucmd, double* resid, int* iters,
-                double* tip, const double* lam0, int n_threads) {
+                double* tip, const double* mlp, int n_threads) {
   Cfg C = load_cfg(cfg);
   Offsets o = offsets(n, nl, seg);
   long long total_nodes = o.node[n];
@@ -522,16 +640,7 @@ int oracle_step(int n, const int* nl, const int* seg, const int* nfix, const dou
     double r = 0.0;
     for (int st = 0; st < n_steps; ++st) {
       int it = 0;
-      std::vector<double> l0;
-      const double* l0p = nullptr;
-      if (lam0 && C.warm == 2) {
-        l0.resize((size_t)C.n_sub * S.N * NK);
-        for (int sb = 0; sb < C.n_sub; ++sb)
-          for (long long j = 0; j < (long long)S.N * NK; ++j)
-            l0[(size_t)sb * S.N * NK + j] = lam0[(size_t)sb * total_nodes * NK + NK * o.node[s] + j];
-        l0p = l0.data();
-      }
-      r = snake_step(S, C, step_index + st, xs, vs, ps, ls, us, &it, l0p);
+      r = snake_step(S, C, step_index + st, xs, vs, ps, ls, us, &it, mlp);
       if (iters) iters[s] = it;
       if (tip) {
         const V3<double>& t = xs[S.N - 1];
@@ -541,6 +650,36 @@ int oracle_step(int n, const int* nl, const int* seg, const int* nfix, const dou
     }
     if (resid) resid[s] = r;
   }
+  return 0;
+}
+
+// Features [nodes][6][24] of every row at the predicted state of substep 0 of env-step
+// step_index, from the current state (which is not modified).
+int oracle_features(int n, const int* nl, const int* seg, const int* nfix, const double* prm,
+                    const double* cfg, long long step_index, const double* x, const double* v,
+                    const double* press, const double* lam, const double* ucmd, double* feat) {
+  Cfg C = load_cfg(cfg);
+  Offsets o = offsets(n, nl, seg);
+  for (int s = 0; s < n; ++s) {
+    Snake<double> S = load_snake<double>(nl, seg, nfix, prm, s);
+    std::vector<V3<double>> X(S.N), V(S.N);
+    for (int i = 0; i < S.N; ++i) {
+      long long g = o.node[s] + i;
+      X[i] = {x[3 * g], x[3 * g + 1], x[3 * g + 2]};
+      V[i] = {v[3 * g], v[3 * g + 1], v[3 * g + 2]};
+    }
+    std::vector<double> P(press + 2 * o.link[s], press + 2 * o.link[s + 1]);
+    std::vector<double> Lm(lam + NK * o.node[s], lam + NK * o.node[s + 1]);
+    int it = 0;
+    snake_step(S, C, step_index, X.data(), V.data(), P.data(), Lm.data(),
+               ucmd ? ucmd + o.link[s] : nullptr, &it, nullptr, feat + (size_t)o.node[s] * NK * kFeat);
+  }
+  return 0;
+}
+
+// Network outputs y[rows] for features [rows][24].
+int oracle_mlp_forward(const double* params, long long rows, const double* feat, double* y) {
+  for (long long r = 0; r < rows; ++r) y[r] = mlp_forward(params, feat + r * kFeat);
   return 0;
 }
 

@@ -20,7 +20,7 @@ class SimConfig(ctypes.Structure):
     _fields_ = [("dt", ctypes.c_double), ("n_sub", ctypes.c_int32), ("iters", ctypes.c_int32),
                 ("tol", ctypes.c_float), ("omega", ctypes.c_float),
                 ("gravity", ctypes.c_float * 3), ("contact", ctypes.c_int32),
-                ("warm", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("warm", ctypes.c_int32), ("beta", ctypes.c_float)]
 
 
 SNAKE_FLOAT_FIELDS = ("L0", "mass", "alpha_s", "alpha_b", "gain", "tau_inf", "tau_def", "mu",
@@ -63,7 +63,22 @@ SIGNATURES = {
     "sim_set_layout": [H, ctypes.c_int, ctypes.c_int, ctypes.c_int],
     "sim_launch_count": [H, I64P],
     "sim_destroy": [H],
+    "sim_set_mlp": [H, H],
+    "sim_snapshot_save": [H],
+    "sim_snapshot_restore": [H],
+    "sim_split_begin": [H],
+    "sim_split_finish": [H],
+    "sim_features": [H, ctypes.POINTER(P), I64P],
+    "mlp_create": [P, ctypes.POINTER(H)],
+    "mlp_set_params": [H, P, ctypes.c_int],
+    "mlp_get_params": [H, P, ctypes.c_int],
+    "mlp_forward": [H, P, ctypes.c_int64, P],
+    "mlp_grad": [H, P, P, ctypes.c_int64, ctypes.c_float, P, P],
+    "mlp_train_step": [H, P, P, ctypes.c_int64, ctypes.c_float, P],
+    "mlp_check": [H],
+    "mlp_destroy": [H],
 }
+MLP_NUM_PARAMS = 19841
 
 
 class SimError(RuntimeError):

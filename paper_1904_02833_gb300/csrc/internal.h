@@ -1,6 +1,7 @@
 // Internal structures shared by the solver kernel and the host runtime.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -29,9 +30,11 @@ struct SolverArgs {
   const int* order;       // snake indices grouped by layout
   int n_items;
   const float* ucmd;      // [links] command override or null
-  const float* lam0;      // learned warm start [n_sub][nodes][6] or null
-  float* lam_log;         // converged multipliers per substep [n_sub][nodes][6] or null
-  long long step_index;
+  const float* lam0;      // learned warm start, normalised multipliers [nodes][6] or null
+  __nv_bfloat16* feat;    // warm-start features [nodes * 6][32] (split mode)
+  int split;              // 0: fused env-steps; 1: one substep boundary per launch
+  int sub;                // split mode: substep to finish (-1: none, begin substep 0)
+  const long long* step_dev;  // device env-step counter (time = counter * dt)
   long long total_nodes;
   int n_steps;
   double h_d;
@@ -43,6 +46,13 @@ struct SolverArgs {
   float g[3];
   int contact;
   int warm;
+  float beta;
 };
+
+// Records the message returned by sim_last_error() on this thread.
+void set_last_error(const char* msg);
+// Enqueues the warm-start network on `feat` [rows][32] -> out [rows] (no synchronisation).
+SimStatus mlp_forward_launch(MlpHandle* h, const void* feat, long long rows, float* out,
+                             cudaStream_t stream);
 
 }  // namespace snakesim

@@ -30,6 +30,12 @@ SimStatus fail(SimStatus s, const std::string& msg) {
   return s;
 }
 
+}  // namespace
+
+void snakesim::set_last_error(const char* msg) { g_err = msg; }
+
+namespace {
+
 #define CU(call)                                                                       \
   do {                                                                                 \
     cudaError_t e_ = (call);                                                           \
@@ -44,9 +50,9 @@ SimStatus fail(SimStatus s, const std::string& msg) {
 // One kernel per nodes-per-lane count (each gets the register budget of its own layout);
 // the host launches the ones that have work on forked streams so that they run together.
 #ifndef SNAKE_MIN_BLOCKS
-#define SNAKE_MIN_BLOCKS 1
+#define SNAKE_MIN_BLOCKS 3
 #endif
-template <int NPL>
+template <int NPL, bool SPLIT>
 __global__ void __launch_bounds__(128, SNAKE_MIN_BLOCKS) snake_solver_kernel(SolverArgs A) {
   const int warp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
@@ -57,15 +63,22 @@ __global__ void __launch_bounds__(128, SNAKE_MIN_BLOCKS) snake_solver_kernel(Sol
     const int gi = lane / G;
     const bool ok = gi < item.y;
     const int snake = ok ? A.order[item.x + gi] : 0;
-    if (G == 8) run_group<NPL, 8>(A, snake, ok);
-    else if (G == 16) run_group<NPL, 16>(A, snake, ok);
-    else run_group<NPL, 32>(A, snake, ok);
+    if (G == 8) run_group<NPL, 8, SPLIT>(A, snake, ok);
+    else if (G == 16) run_group<NPL, 16, SPLIT>(A, snake, ok);
+    else run_group<NPL, 32, SPLIT>(A, snake, ok);
   }
 }
 
 typedef void (*SolverKernel)(SolverArgs);
-const SolverKernel kSolverKernels[4] = {snake_solver_kernel<1>, snake_solver_kernel<2>,
-                                        snake_solver_kernel<3>, snake_solver_kernel<4>};
+// [split][nodes per lane - 1]
+const SolverKernel kSolverKernels[2][4] = {
+    {snake_solver_kernel<1, false>, snake_solver_kernel<2, false>, snake_solver_kernel<3, false>,
+     snake_solver_kernel<4, false>},
+    {snake_solver_kernel<1, true>, snake_solver_kernel<2, true>, snake_solver_kernel<3, true>,
+     snake_solver_kernel<4, true>}};
+
+// Advances the device env-step counter once all solver launches of a step are done.
+__global__ void advance_step_kernel(long long* step, int n) { *step += n; }
 
 __global__ void pack_xyz_kernel(const float4* __restrict__ in, float* __restrict__ out, long long n) {
   long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -110,14 +123,26 @@ struct SimHandle {
   bool use_ucmd = false;
   float* inv_mass_d = nullptr;
   float* scratch3 = nullptr;  // [nodes * 6] staging for layout conversions
-  float* lam0 = nullptr;      // optional learned warm start
-  float* lam_log = nullptr;   // optional per-substep multiplier log
-  long long step_index = 0;
+  float* lam0 = nullptr;            // network output, normalised multipliers [nodes][6]
+  __nv_bfloat16* feat = nullptr;   // features [nodes * 6][32]
+  MlpHandle* mlp = nullptr;
+  int cur_sub = -1;                // split stepping: substep begun, -1 at a step boundary
+  // snapshot
+  float4 *snap_pos = nullptr, *snap_vel = nullptr;
+  float2* snap_press = nullptr;
+  float* snap_lam = nullptr;
+  long long snap_step = 0;
+  long long* snap_step_dev = nullptr;
+  int snap_sub = -1;
+  bool snap_valid = false;
+  long long step_index = 0;        // host mirror of the device counter
+  long long* step_dev = nullptr;   // device env-step counter read by the kernels
   long long launches = 0;
   std::map<int, int> layout;  // node count -> layout id
   int grid = 0;
   cudaGraphExec_t graph = nullptr;
   int graph_steps = -1;
+  long long graph_launches = 0;
   bool graph_dirty = true;
 };
 
@@ -126,8 +151,9 @@ namespace {
 SimStatus validate_cfg(const SimConfig* c) {
   if (!c) return fail(SIM_EINVAL, "null config");
   if (!(c->dt > 0.0) || c->n_sub < 1 || c->iters < 0 || !(c->tol >= 0.f) || !(c->omega > 0.f) ||
-      c->warm < 0 || c->warm > 2)
-    return fail(SIM_EINVAL, "invalid config (dt > 0, n_sub >= 1, iters >= 0, tol >= 0, omega > 0, warm in 0..2)");
+      c->warm < 0 || c->warm > 2 || !(c->beta >= 0.f && c->beta <= 1.f))
+    return fail(SIM_EINVAL, "invalid config (dt > 0, n_sub >= 1, iters >= 0, tol >= 0, omega > 0, "
+                            "warm in 0..2, beta in [0, 1])");
   return SIM_OK;
 }
 
@@ -189,7 +215,7 @@ SimStatus build_items(SimHandle* h, const std::map<int, int>* only_bucket = null
   CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   for (int p = 0; p < 4; ++p) {
     int per_sm = 0;
-    CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kSolverKernels[p], 128, 0));
+    CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kSolverKernels[0][p], 128, 0));
     const int n = h->npl_first[p + 1] - h->npl_first[p];
     const int need = (n + 3) / 4;
     h->npl_grid[p] = n == 0 ? 0 : std::max(1, std::min(need, std::max(1, per_sm) * sms));
@@ -206,8 +232,10 @@ SolverArgs make_args(SimHandle* h, int n_steps) {
   A.items = h->items; A.order = h->order; A.n_items = h->n_items;
   A.ucmd = h->use_ucmd ? h->ucmd : nullptr;
   A.lam0 = (h->cfg.warm == SIM_WARM_LEARNED) ? h->lam0 : nullptr;
-  A.lam_log = h->lam_log;
-  A.step_index = h->step_index;
+  A.feat = h->feat;
+  A.split = 0;
+  A.sub = -1;
+  A.step_dev = h->step_dev;
   A.total_nodes = h->n_nodes;
   A.n_steps = n_steps;
   A.h_d = h->cfg.dt / h->cfg.n_sub;
@@ -219,12 +247,58 @@ SolverArgs make_args(SimHandle* h, int n_steps) {
   A.g[0] = h->cfg.gravity[0]; A.g[1] = h->cfg.gravity[1]; A.g[2] = h->cfg.gravity[2];
   A.contact = h->cfg.contact;
   A.warm = h->cfg.warm;
+  A.beta = h->cfg.beta;
   return A;
 }
 
+SimStatus launch_args(SimHandle* h, const SolverArgs& A, cudaStream_t st);
+
+// Split mode: finish substep `sub` (if >= 0) and begin the next one.
+SimStatus launch_split(SimHandle* h, int sub, cudaStream_t st) {
+  SolverArgs A = make_args(h, 0);
+  A.split = 1;
+  A.sub = sub;
+  return launch_args(h, A, st);
+}
+
+SimStatus advance(SimHandle* h, int n, cudaStream_t st) {
+  advance_step_kernel<<<1, 1, 0, st>>>(h->step_dev, n);
+  CU(cudaGetLastError());
+  h->launches += 1;
+  return SIM_OK;
+}
+
+// One env-step substep by substep, with the network between solver launches.
+SimStatus split_step(SimHandle* h, cudaStream_t st) {
+  SimStatus r = launch_split(h, -1, st);
+  for (int s = 0; s < h->cfg.n_sub && r == SIM_OK; ++s) {
+    if (h->cfg.warm == SIM_WARM_LEARNED) {
+      r = mlp_forward_launch(h->mlp, h->feat, h->n_nodes * 6, h->lam0, st);
+      h->launches += 1;
+    }
+    if (r == SIM_OK) r = launch_split(h, s, st);
+  }
+  if (r == SIM_OK) r = advance(h, 1, st);
+  return r;
+}
+
+// Enqueues n_steps env-steps (device counter advanced by the last launch).
 SimStatus launch_steps(SimHandle* h, int n_steps, cudaStream_t st) {
   if (n_steps <= 0 || h->n_items == 0) return SIM_OK;
-  SolverArgs A = make_args(h, n_steps);
+  if (h->cfg.warm == SIM_WARM_LEARNED) {
+    for (int k = 0; k < n_steps; ++k) {
+      SimStatus r = split_step(h, st);
+      if (r != SIM_OK) return r;
+    }
+    return SIM_OK;
+  }
+  SimStatus r = launch_args(h, make_args(h, n_steps), st);
+  if (r == SIM_OK) r = advance(h, n_steps, st);
+  return r;
+}
+
+SimStatus launch_args(SimHandle* h, const SolverArgs& A, cudaStream_t st) {
+  if (h->n_items == 0) return SIM_OK;
   int kinds = 0;
   for (int p = 0; p < 4; ++p) kinds += h->npl_grid[p] > 0;
   bool fork = kinds > 1;
@@ -236,7 +310,7 @@ SimStatus launch_steps(SimHandle* h, int n_steps, cudaStream_t st) {
     B.n_items = h->npl_first[p + 1] - h->npl_first[p];
     cudaStream_t s = fork ? h->side[p] : st;
     if (fork) CU(cudaStreamWaitEvent(s, h->ev_fork, 0));
-    kSolverKernels[p]<<<h->npl_grid[p], 128, 0, s>>>(B);
+    kSolverKernels[A.split ? 1 : 0][p]<<<h->npl_grid[p], 128, 0, s>>>(B);
     CU(cudaGetLastError());
     h->launches += 1;
     if (fork) {
@@ -315,6 +389,9 @@ SimStatus sim_create(const SimConfig* cfg, int n_snakes, const SnakeParams* para
   ALLOC(h->ucmd, std::max<long long>(1, h->n_links) * sizeof(float));
   ALLOC(h->inv_mass_d, h->n_nodes * sizeof(float));
   ALLOC(h->scratch3, h->n_nodes * 6 * sizeof(float));
+  ALLOC(h->lam0, h->n_nodes * 6 * sizeof(float));
+  ALLOC(h->step_dev, sizeof(long long));
+  ALLOC(h->feat, h->n_nodes * 6 * 32 * sizeof(__nv_bfloat16));
 #undef ALLOC
 #define CUC(call)                                                                         \
   e = (call);                                                                             \
@@ -329,6 +406,7 @@ SimStatus sim_create(const SimConfig* cfg, int n_snakes, const SnakeParams* para
   CUC(cudaMemset(h->resid, 0, n_snakes * sizeof(float)));
   CUC(cudaMemset(h->iters, 0, n_snakes * sizeof(int)));
   CUC(cudaMemset(h->status, 0, n_snakes * sizeof(int)));
+  CUC(cudaMemset(h->step_dev, 0, sizeof(long long)));
   CUC(cudaMemcpy(h->inv_mass_d, h->inv_mass_h.data(), h->n_nodes * sizeof(float), cudaMemcpyHostToDevice));
   CUC(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
   CUC(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
@@ -367,8 +445,9 @@ SimStatus sim_set_pressure(SimHandle* h, const float* u, int is_device) {
 SimStatus sim_step(SimHandle* h, int n_steps) {
   if (!h) return fail(SIM_EINVAL, "null handle");
   if (n_steps < 0) return fail(SIM_EINVAL, "n_steps < 0");
-  if (h->cfg.warm == SIM_WARM_LEARNED && !h->lam0)
-    return fail(SIM_EINVAL, "learned warm start requested but no warm-start multipliers were provided");
+  if (h->cfg.warm == SIM_WARM_LEARNED && !h->mlp)
+    return fail(SIM_EINVAL, "learned warm start requested but no network is attached (sim_set_mlp)");
+  if (h->cur_sub >= 0) return fail(SIM_EINVAL, "a split env-step is in progress (sim_split_finish)");
   SimStatus st = launch_steps(h, n_steps, h->stream);
   if (st != SIM_OK) return st;
   h->step_index += n_steps;
@@ -378,37 +457,37 @@ SimStatus sim_step(SimHandle* h, int n_steps) {
 SimStatus sim_step_graph(SimHandle* h, int n_steps) {
   if (!h) return fail(SIM_EINVAL, "null handle");
   if (n_steps < 0) return fail(SIM_EINVAL, "n_steps < 0");
-  // The captured kernel reads its step counter from the launch arguments, so the graph
-  // is re-instantiated whenever the counter or the configuration changes; the update
-  // path below patches only the arguments of the existing kernel node.
+  if (h->cfg.warm == SIM_WARM_LEARNED && !h->mlp)
+    return fail(SIM_EINVAL, "learned warm start requested but no network is attached (sim_set_mlp)");
+  if (h->cur_sub >= 0) return fail(SIM_EINVAL, "a split env-step is in progress (sim_split_finish)");
+  if (n_steps == 0) return SIM_OK;
+  // The kernels read the env-step counter from device memory and the graph's last node
+  // advances it, so one captured graph per (configuration, layout, n_steps) is replayed
+  // unchanged; it is captured on a private stream forked from the handle's stream.
+  if (!h->graph || h->graph_dirty || h->graph_steps != n_steps) {
+    if (h->graph) { cudaGraphExecDestroy(h->graph); h->graph = nullptr; }
+    cudaGraph_t g = nullptr;
+    CU(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+    const long long launches0 = h->launches;
+    SimStatus st = launch_steps(h, n_steps, h->cap_stream);
+    cudaError_t ce = cudaStreamEndCapture(h->cap_stream, &g);
+    if (st != SIM_OK) { h->launches = launches0; if (g) cudaGraphDestroy(g); return st; }
+    if (ce != cudaSuccess) return fail(SIM_ECUDA, std::string("capture: ") + cudaGetErrorString(ce));
+    ce = cudaGraphInstantiate(&h->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (ce != cudaSuccess) { h->graph = nullptr; return fail(SIM_ECUDA, std::string("instantiate: ") + cudaGetErrorString(ce)); }
+    h->graph_steps = n_steps;
+    h->graph_dirty = false;
+    // kernel launches per replay (counted while capturing)
+    h->graph_launches = h->launches - launches0;
+    h->launches = launches0;
+  }
   CU(cudaEventRecord(h->ev_fork, h->stream));
   CU(cudaStreamWaitEvent(h->cap_stream, h->ev_fork, 0));
-  cudaGraph_t g = nullptr;
-  CU(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
-  long long launches0 = h->launches;
-  SimStatus st = launch_steps(h, n_steps, h->cap_stream);
-  cudaError_t ce = cudaStreamEndCapture(h->cap_stream, &g);
-  if (st != SIM_OK) { if (g) cudaGraphDestroy(g); return st; }
-  if (ce != cudaSuccess) return fail(SIM_ECUDA, std::string("capture: ") + cudaGetErrorString(ce));
-  bool updated = false;
-  if (h->graph && !h->graph_dirty && h->graph_steps == n_steps) {
-    cudaGraphExecUpdateResultInfo info;
-    if (cudaGraphExecUpdate(h->graph, g, &info) == cudaSuccess) updated = true;
-    else cudaGetLastError();
-  }
-  if (!updated) {
-    if (h->graph) cudaGraphExecDestroy(h->graph);
-    h->graph = nullptr;
-    ce = cudaGraphInstantiate(&h->graph, g, 0);
-    if (ce != cudaSuccess) { cudaGraphDestroy(g); return fail(SIM_ECUDA, std::string("instantiate: ") + cudaGetErrorString(ce)); }
-  }
-  cudaGraphDestroy(g);
-  h->graph_steps = n_steps;
-  h->graph_dirty = false;
   CU(cudaGraphLaunch(h->graph, h->cap_stream));
   CU(cudaEventRecord(h->ev_join, h->cap_stream));
   CU(cudaStreamWaitEvent(h->stream, h->ev_join, 0));
-  (void)launches0;
+  h->launches += h->graph_launches;
   h->step_index += n_steps;
   return SIM_OK;
 }
@@ -485,6 +564,9 @@ SimStatus sim_get_info(SimHandle* h, int64_t* n_nodes, int64_t* n_links, int32_t
 SimStatus sim_set_step_index(SimHandle* h, int64_t step_index) {
   if (!h) return fail(SIM_EINVAL, "null handle");
   h->step_index = step_index;
+  long long v = step_index;
+  CU(cudaMemcpyAsync(h->step_dev, &v, sizeof(long long), cudaMemcpyHostToDevice, h->stream));
+  CU(cudaStreamSynchronize(h->stream));
   return SIM_OK;
 }
 
@@ -546,7 +628,9 @@ SimStatus sim_autotune(SimHandle* h, int n_steps) {
     CU(cudaMemcpyAsync(l0, h->lam, n * 6 * sizeof(float), cudaMemcpyDeviceToDevice, h->stream));
     return SIM_OK;
   };
+  const long long step_keep = h->step_index;
   auto restore = [&]() -> SimStatus {
+    CU(cudaMemcpyAsync(h->step_dev, &step_keep, sizeof(long long), cudaMemcpyHostToDevice, h->stream));
     CU(cudaMemcpyAsync(h->pos, p0, n * sizeof(float4), cudaMemcpyDeviceToDevice, h->stream));
     CU(cudaMemcpyAsync(h->vel, v0, n * sizeof(float4), cudaMemcpyDeviceToDevice, h->stream));
     CU(cudaMemcpyAsync(h->press, pr0, h->n_links * sizeof(float2), cudaMemcpyDeviceToDevice, h->stream));
@@ -598,6 +682,85 @@ SimStatus sim_autotune(SimHandle* h, int n_steps) {
   return build_items(h);
 }
 
+SimStatus sim_set_mlp(SimHandle* h, MlpHandle* m) {
+  if (!h) return fail(SIM_EINVAL, "null handle");
+  h->mlp = m;
+  h->graph_dirty = true;
+  return SIM_OK;
+}
+
+SimStatus sim_split_begin(SimHandle* h) {
+  if (!h) return fail(SIM_EINVAL, "null handle");
+  if (h->cur_sub >= 0) return fail(SIM_EINVAL, "an env-step is already in progress");
+  SimStatus st = launch_split(h, -1, h->stream);
+  if (st != SIM_OK) return st;
+  h->cur_sub = 0;
+  return SIM_OK;
+}
+
+SimStatus sim_split_finish(SimHandle* h) {
+  if (!h) return fail(SIM_EINVAL, "null handle");
+  if (h->cur_sub < 0) return fail(SIM_EINVAL, "no env-step in progress (sim_split_begin)");
+  if (h->cfg.warm == SIM_WARM_LEARNED) {
+    if (!h->mlp) return fail(SIM_EINVAL, "learned warm start without a network (sim_set_mlp)");
+    SimStatus r = mlp_forward_launch(h->mlp, h->feat, h->n_nodes * 6, h->lam0, h->stream);
+    if (r != SIM_OK) return r;
+    h->launches += 1;
+  }
+  SimStatus st = launch_split(h, h->cur_sub, h->stream);
+  if (st != SIM_OK) return st;
+  h->cur_sub += 1;
+  if (h->cur_sub >= h->cfg.n_sub) {
+    st = advance(h, 1, h->stream);
+    if (st != SIM_OK) return st;
+    h->cur_sub = -1;
+    h->step_index += 1;
+  }
+  return SIM_OK;
+}
+
+SimStatus sim_features(SimHandle* h, void** feat, int64_t* rows) {
+  if (!h) return fail(SIM_EINVAL, "null handle");
+  if (feat) *feat = h->feat;
+  if (rows) *rows = h->n_nodes * 6;
+  return SIM_OK;
+}
+
+SimStatus sim_snapshot_save(SimHandle* h) {
+  if (!h) return fail(SIM_EINVAL, "null handle");
+  const long long n = h->n_nodes;
+  if (!h->snap_pos) {
+    CU(cudaMalloc(&h->snap_pos, n * sizeof(float4)));
+    CU(cudaMalloc(&h->snap_vel, n * sizeof(float4)));
+    CU(cudaMalloc(&h->snap_press, h->n_links * sizeof(float2)));
+    CU(cudaMalloc(&h->snap_lam, n * 6 * sizeof(float)));
+    CU(cudaMalloc(&h->snap_step_dev, sizeof(long long)));
+  }
+  CU(cudaMemcpyAsync(h->snap_step_dev, h->step_dev, sizeof(long long), cudaMemcpyDeviceToDevice, h->stream));
+  CU(cudaMemcpyAsync(h->snap_pos, h->pos, n * sizeof(float4), cudaMemcpyDeviceToDevice, h->stream));
+  CU(cudaMemcpyAsync(h->snap_vel, h->vel, n * sizeof(float4), cudaMemcpyDeviceToDevice, h->stream));
+  CU(cudaMemcpyAsync(h->snap_press, h->press, h->n_links * sizeof(float2), cudaMemcpyDeviceToDevice, h->stream));
+  CU(cudaMemcpyAsync(h->snap_lam, h->lam, n * 6 * sizeof(float), cudaMemcpyDeviceToDevice, h->stream));
+  h->snap_step = h->step_index;
+  h->snap_sub = h->cur_sub;
+  h->snap_valid = true;
+  return SIM_OK;
+}
+
+SimStatus sim_snapshot_restore(SimHandle* h) {
+  if (!h) return fail(SIM_EINVAL, "null handle");
+  if (!h->snap_valid) return fail(SIM_EINVAL, "no snapshot saved");
+  const long long n = h->n_nodes;
+  CU(cudaMemcpyAsync(h->pos, h->snap_pos, n * sizeof(float4), cudaMemcpyDeviceToDevice, h->stream));
+  CU(cudaMemcpyAsync(h->vel, h->snap_vel, n * sizeof(float4), cudaMemcpyDeviceToDevice, h->stream));
+  CU(cudaMemcpyAsync(h->press, h->snap_press, h->n_links * sizeof(float2), cudaMemcpyDeviceToDevice, h->stream));
+  CU(cudaMemcpyAsync(h->lam, h->snap_lam, n * 6 * sizeof(float), cudaMemcpyDeviceToDevice, h->stream));
+  CU(cudaMemcpyAsync(h->step_dev, h->snap_step_dev, sizeof(long long), cudaMemcpyDeviceToDevice, h->stream));
+  h->step_index = h->snap_step;
+  h->cur_sub = h->snap_sub;
+  return SIM_OK;
+}
+
 SimStatus sim_launch_count(SimHandle* h, int64_t* launches) {
   if (!h || !launches) return fail(SIM_EINVAL, "null handle or output");
   *launches = h->launches;
@@ -617,7 +780,8 @@ SimStatus sim_destroy(SimHandle* h) {
   }
   void* ptrs[] = {h->pos, h->vel, h->press, h->lam, h->prm, h->node_off_d, h->link_off_d, h->resid,
                   h->iters, h->status, h->items, h->order, h->ucmd, h->inv_mass_d, h->scratch3,
-                  h->lam0, h->lam_log};
+                  h->lam0, h->feat, h->snap_pos, h->snap_vel, h->snap_press, h->snap_lam,
+                  h->step_dev, h->snap_step_dev};
   for (void* p : ptrs) if (p) cudaFree(p);
   delete h;
   return SIM_OK;

@@ -29,6 +29,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <cuda_bf16.h>
+
 #include "internal.h"
 
 namespace snakesim {
@@ -279,8 +281,121 @@ __device__ __forceinline__ float row_pass(const SnakeK& S, const SolverArgs& A, 
   return r;
 }
 
-// Advances the snake owned by this lane group by A.n_steps env-steps.
+// Writes the 24 warm-start features (padded to 32, bf16) of the six rows each node owns,
+// at the predicted positions of the substep start.  Row frame: horizontal unit tangent
+// t (stretch: its own segment; bend: the incoming segment; contact: the outgoing one;
+// friction x / y: world x / y), b = z x t, z.  Features: one-hot row kind (6); height of
+// the row's first node above its contact height / L0 (1); positions of the row's second
+// and third node relative to the first, in the frame, / L0 (6); velocities of the up to
+// three nodes in the frame, x h / L0 (9); rest angle of a yaw row (1); the row's
+// multiplier from the previous substep / (m g h^2) (1).  Rows that do not exist are zero.
 template <int NPL, int G>
+__device__ __forceinline__ void write_features(const SnakeK& S, const SolverArgs& A, int q, bool valid,
+                                               const float (&xs)[NPL][3], const float (&dx)[NPL][3],
+                                               const float (&v)[NPL][3], const float (&lam)[NPL][6],
+                                               const float (&th)[NPL]) {
+  float nl[9], nr[9];  // left / right neighbour: xs, dx, v
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    nl[d] = __shfl_up_sync(kFull, xs[NPL - 1][d], 1, G);
+    nl[3 + d] = __shfl_up_sync(kFull, dx[NPL - 1][d], 1, G);
+    nl[6 + d] = __shfl_up_sync(kFull, v[NPL - 1][d], 1, G);
+    nr[d] = __shfl_down_sync(kFull, xs[0][d], 1, G);
+    nr[3 + d] = __shfl_down_sync(kFull, dx[0][d], 1, G);
+    nr[6 + d] = __shfl_down_sync(kFull, v[0][d], 1, G);
+  }
+  if (!valid) return;
+  const float lsc = 1.0f / (S.mass * 9.81f * A.h * A.h);
+  const float hl = A.h * S.inv_L0;
+#pragma unroll
+  for (int j = 0; j < NPL; ++j) {
+    const int i = q * NPL + j;
+    if (i >= S.N) continue;
+    // nodes i-1, i, i+1: substep-start position, displacement, velocity
+    float X[3][3], D[3][3], V[3][3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      X[1][d] = xs[j][d]; D[1][d] = dx[j][d]; V[1][d] = v[j][d];
+      if (j > 0) { X[0][d] = xs[j - 1][d]; D[0][d] = dx[j - 1][d]; V[0][d] = v[j - 1][d]; }
+      else { X[0][d] = nl[d]; D[0][d] = nl[3 + d]; V[0][d] = nl[6 + d]; }
+      if (j + 1 < NPL) { X[2][d] = xs[j + 1][d]; D[2][d] = dx[j + 1][d]; V[2][d] = v[j + 1][d]; }
+      else { X[2][d] = nr[d]; D[2][d] = nr[3 + d]; V[2][d] = nr[6 + d]; }
+    }
+    auto rel = [&](int b, int a, int d) { return (X[b][d] - X[a][d]) + (D[b][d] - D[a][d]); };
+    auto dirh = [&](int b, int a, float& tx, float& ty) {
+      const float ex = rel(b, a, 0), ey = rel(b, a, 1);
+      const float n2 = ex * ex + ey * ey;
+      if (n2 > 0.f) { const float in = rsqrtf(n2); tx = ex * in; ty = ey * in; }
+      else { tx = 1.f; ty = 0.f; }
+    };
+    const bool has_next = i + 1 <= S.N - 1, has_prev = i >= 1;
+    const bool free_i = i >= S.nfix;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      float f[32];
+#pragma unroll
+      for (int c = 0; c < 32; ++c) f[c] = 0.f;
+      bool ex;
+      if (k == 0) ex = has_next;
+      else if (k <= 2) ex = has_prev && has_next;
+      else ex = A.contact && free_i;
+      if (ex) {
+        f[k] = 1.f;
+        int na, nb = -1, nc = -1;  // local node indices 0..2 (i-1, i, i+1)
+        float tx, ty;
+        if (k == 0) { na = 1; nb = 2; dirh(2, 1, tx, ty); }
+        else if (k <= 2) { na = 0; nb = 1; nc = 2; dirh(1, 0, tx, ty); }
+        else {
+          na = 1;
+          if (k == 3) { if (has_next) dirh(2, 1, tx, ty); else dirh(1, 0, tx, ty); }
+          else if (k == 4) { tx = 1.f; ty = 0.f; }
+          else { tx = 0.f; ty = 1.f; }
+        }
+        f[6] = ((X[na][2] - S.radius) + D[na][2]) * S.inv_L0;
+        if (nb >= 0) {
+          const float ux = rel(nb, na, 0), uy = rel(nb, na, 1), uz = rel(nb, na, 2);
+          f[7] = (ux * tx + uy * ty) * S.inv_L0;
+          f[8] = (-ux * ty + uy * tx) * S.inv_L0;
+          f[9] = uz * S.inv_L0;
+        }
+        if (nc >= 0) {
+          const float ux = rel(nc, na, 0), uy = rel(nc, na, 1), uz = rel(nc, na, 2);
+          f[10] = (ux * tx + uy * ty) * S.inv_L0;
+          f[11] = (-ux * ty + uy * tx) * S.inv_L0;
+          f[12] = uz * S.inv_L0;
+        }
+        const int nodes[3] = {na, nb, nc};
+#pragma unroll
+        for (int u = 0; u < 3; ++u) {
+          if (nodes[u] < 0) continue;
+          const int n = nodes[u];
+          f[13 + 3 * u] = (V[n][0] * tx + V[n][1] * ty) * hl;
+          f[14 + 3 * u] = (-V[n][0] * ty + V[n][1] * tx) * hl;
+          f[15 + 3 * u] = V[n][2] * hl;
+        }
+        if (k == 1) f[22] = th[j];
+        f[23] = lam[j][k] * lsc;
+      }
+      uint32_t pk[16];
+#pragma unroll
+      for (int c = 0; c < 16; ++c) {
+        __nv_bfloat162 b2 = __floats2bfloat162_rn(f[2 * c], f[2 * c + 1]);
+        pk[c] = *reinterpret_cast<uint32_t*>(&b2);
+      }
+      uint4* dst = reinterpret_cast<uint4*>(A.feat + ((size_t)(S.nb + i) * 6 + k) * 32);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) dst[c] = make_uint4(pk[4 * c], pk[4 * c + 1], pk[4 * c + 2], pk[4 * c + 3]);
+    }
+  }
+}
+
+// Advances the snake owned by this lane group.  Fused mode (A.split == 0): A.n_steps
+// env-steps with all substeps in registers.  Split mode: finishes substep A.sub (if >= 0)
+// of the current env-step and, if A.sub + 1 < n_sub, begins substep A.sub + 1 (gait,
+// filter, prediction), writes its features and leaves the state in HBM at that point
+// (positions = substep start, velocities = predicted), so that the warm-start network
+// can run between two launches.
+template <int NPL, int G, bool SPLIT>
 __device__ void run_group(const SolverArgs& A, int snake, bool valid) {
   const int lane = threadIdx.x & 31;
   const int q = lane & (G - 1);
@@ -302,6 +417,7 @@ __device__ void run_group(const SolverArgs& A, int snake, bool valid) {
 
   // x = xs + dx; between substeps dx holds the last substep's displacement
   float xs[NPL][3], dx[NPL][3], v[NPL][3], lam[NPL][6], pR[NPL], pL[NPL], th[NPL];
+  const bool mid = SPLIT && A.sub >= 0;  // HBM holds a begun substep
 #pragma unroll
   for (int j = 0; j < NPL; ++j) {
     const int i = q * NPL + j;
@@ -317,6 +433,10 @@ __device__ void run_group(const SolverArgs& A, int snake, bool valid) {
       const int kl = min(i / S.seg, S.L - 1);
       const float2 pp = A.press[S.lb + kl];
       pR[j] = pp.x; pL[j] = pp.y;
+      if (mid) {
+        if (i >= S.nfix) { dx[j][0] = h * v[j][0]; dx[j][1] = h * v[j][1]; dx[j][2] = h * v[j][2]; }
+        th[j] = (i % S.seg == 0) ? 0.f : S.gain * (pR[j] - pL[j]) * S.L0;
+      }
     } else {
       xs[j][0] = xs[j][1] = xs[j][2] = 0.f;
       v[j][0] = v[j][1] = v[j][2] = 0.f;
@@ -326,115 +446,123 @@ __device__ void run_group(const SolverArgs& A, int snake, bool valid) {
     }
   }
 
-  float rmax = 0.f;
-  int itot = 0;
-  for (int st = 0; st < A.n_steps; ++st) {
-    rmax = 0.f;
-    itot = 0;
-    for (int s = 0; s < A.n_sub; ++s) {
-      // (a1) gait target at the end of the substep, (a2) chamber latency, (a3) rest angle
-      const double tp = ((double)(A.step_index + st) * A.n_sub + (double)(s + 1)) * A.h_d;
-      double cyc = (double)P.gait_freq * tp;
-      cyc -= floor(cyc);
-      const float phase = 6.283185307179586f * (float)cyc;
+  // (a1) gait target at the end of substep s, (a2) chamber latency, (a3) rest angle,
+  // (a4) predict: the substep starts at x = xs + dx; dx restarts at h v
+  auto begin_substep = [&](long long step, int s) {
+    const double tp = ((double)step * A.n_sub + (double)(s + 1)) * A.h_d;
+    double cyc = (double)P.gait_freq * tp;
+    cyc -= floor(cyc);
+    const float phase = 6.283185307179586f * (float)cyc;
 #pragma unroll
-      for (int j = 0; j < NPL; ++j) {
-        const int i = q * NPL + j;
-        if (!(valid && i < S.N)) continue;
-        const int kl = min(i / S.seg, S.L - 1);
-        float u;
-        if (A.ucmd) {
-          u = A.ucmd[S.lb + kl];
-        } else {
-          float a = P.gait_offset + P.gait_scale * sinf(phase + (float)kl * P.gait_lag);
-          a = fminf(1.f, fmaxf(-1.f, a)) * P.gait_amp;
-          if (P.gait_alternate != 0.f && (kl & 1)) a = -a;
-          u = a;
-        }
-        const float tR = fmaxf(u, 0.f), tL = fmaxf(-u, 0.f);
-        pR[j] = tR + (pR[j] - tR) * (tR > pR[j] ? S.e_inf : S.e_def);
-        pL[j] = tL + (pL[j] - tL) * (tL > pL[j] ? S.e_inf : S.e_def);
-        th[j] = (i % S.seg == 0) ? 0.f : S.gain * (pR[j] - pL[j]) * S.L0;
-      }
-      // (a4) predict: the substep starts at x = xs + dx; dx restarts at h v
-#pragma unroll
-      for (int j = 0; j < NPL; ++j) {
-        const int i = q * NPL + j;
-        xs[j][0] += dx[j][0]; xs[j][1] += dx[j][1]; xs[j][2] += dx[j][2];
-        dx[j][0] = dx[j][1] = dx[j][2] = 0.f;
-        if (valid && i < S.N && i >= S.nfix) {
-          v[j][0] += h * A.g[0]; v[j][1] += h * A.g[1]; v[j][2] += h * A.g[2];
-          dx[j][0] = h * v[j][0]; dx[j][1] = h * v[j][1]; dx[j][2] = h * v[j][2];
-        }
-      }
-      // substep-start positions of the neighbours across the lane boundary
-      float xsl[3], xsr[3];
-#pragma unroll
-      for (int d = 0; d < 3; ++d) {
-        xsl[d] = __shfl_up_sync(kFull, xs[NPL - 1][d], 1, G);
-        xsr[d] = __shfl_down_sync(kFull, xs[0][d], 1, G);
-      }
-      // multipliers at the start of the substep
-      bool stop;
-      if (A.warm == 0) {
-#pragma unroll
-        for (int j = 0; j < NPL; ++j)
-#pragma unroll
-          for (int k = 0; k < 6; ++k) lam[j][k] = 0.f;
+    for (int j = 0; j < NPL; ++j) {
+      const int i = q * NPL + j;
+      if (!(valid && i < S.N)) continue;
+      const int kl = min(i / S.seg, S.L - 1);
+      float u;
+      if (A.ucmd) {
+        u = A.ucmd[S.lb + kl];
       } else {
-        if (A.warm == 2 && A.lam0) {
-#pragma unroll
-          for (int j = 0; j < NPL; ++j) {
-            const int i = q * NPL + j;
-            if (valid && i < S.N)
-#pragma unroll
-              for (int k = 0; k < 6; ++k)
-                lam[j][k] = A.lam0[((size_t)s * A.total_nodes + S.nb + i) * 6 + k];
-          }
-        }
-        row_pass<NPL, G, true>(S, A, q, valid, 0, xs, dx, xsl, xsr, lam, th, stop);
+        float a = P.gait_offset + P.gait_scale * sinf(phase + (float)kl * P.gait_lag);
+        a = fminf(1.f, fmaxf(-1.f, a)) * P.gait_amp;
+        if (P.gait_alternate != 0.f && (kl & 1)) a = -a;
+        u = a;
       }
-      // (a5, a6) Jacobi iterations until the residual reaches tol or the cap
-      bool done = !valid;
-      float rs = 0.f;
-      int ks = 0;
-      for (int k = 0;; ++k) {
-        const float r = row_pass<NPL, G, false>(S, A, q, !done, k, xs, dx, xsl, xsr, lam, th, stop);
-        if (!done && stop) { done = true; rs = r; ks = k; }
-        if (__all_sync(kFull, done)) break;
+      const float tR = fmaxf(u, 0.f), tL = fmaxf(-u, 0.f);
+      pR[j] = tR + (pR[j] - tR) * (tR > pR[j] ? S.e_inf : S.e_def);
+      pL[j] = tL + (pL[j] - tL) * (tL > pL[j] ? S.e_inf : S.e_def);
+      th[j] = (i % S.seg == 0) ? 0.f : S.gain * (pR[j] - pL[j]) * S.L0;
+    }
+#pragma unroll
+    for (int j = 0; j < NPL; ++j) {
+      const int i = q * NPL + j;
+      xs[j][0] += dx[j][0]; xs[j][1] += dx[j][1]; xs[j][2] += dx[j][2];
+      dx[j][0] = dx[j][1] = dx[j][2] = 0.f;
+      if (valid && i < S.N && i >= S.nfix) {
+        v[j][0] += h * A.g[0]; v[j][1] += h * A.g[1]; v[j][2] += h * A.g[2];
+        dx[j][0] = h * v[j][0]; dx[j][1] = h * v[j][1]; dx[j][2] = h * v[j][2];
       }
-      // a non-finite displacement anywhere in the snake marks the step (fmaxf drops NaN)
-      float bad = 0.f;
+    }
+  };
+
+  // warm start, (a5, a6) Jacobi iterations, (a7) velocity with damping
+  auto finish_substep = [&](float& rmax, int& itot) {
+    float xsl[3], xsr[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      xsl[d] = __shfl_up_sync(kFull, xs[NPL - 1][d], 1, G);
+      xsr[d] = __shfl_down_sync(kFull, xs[0][d], 1, G);
+    }
+    bool stop;
+    if (A.warm == 0) {
 #pragma unroll
       for (int j = 0; j < NPL; ++j)
-        if (!(fabsf(dx[j][0]) + fabsf(dx[j][1]) + fabsf(dx[j][2]) <= 3.0e38f)) bad = 1.f;
-      bad = group_max<G>(bad);
-      rmax = fmaxf(rmax, rs);
-      if (!(rs <= 3.0e38f) || bad > 0.f) rmax = INFINITY;
-      itot += ks;
-      // (a7) velocity from the substep displacement with exponential damping
+#pragma unroll
+        for (int k = 0; k < 6; ++k) lam[j][k] = 0.f;
+    } else {
+      // warm start: beta lambda_prev (+ m g h^2 y of the network)
+      const float sc = S.mass * 9.81f * h * h;
 #pragma unroll
       for (int j = 0; j < NPL; ++j) {
         const int i = q * NPL + j;
-        if (valid && i < S.N && i >= S.nfix) {
-          v[j][0] = dx[j][0] * S.damp_over_h;
-          v[j][1] = dx[j][1] * S.damp_over_h;
-          v[j][2] = dx[j][2] * S.damp_over_h;
-        } else {
-          v[j][0] = v[j][1] = v[j][2] = 0.f;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+          float l = A.beta * lam[j][k];
+          if (A.warm == 2 && A.lam0 && valid && i < S.N) l += A.lam0[(size_t)(S.nb + i) * 6 + k] * sc;
+          lam[j][k] = l;
         }
       }
-      if (A.lam_log && valid) {
-        // per-substep converged multipliers (training data of the warm start)
+      row_pass<NPL, G, true>(S, A, q, valid, 0, xs, dx, xsl, xsr, lam, th, stop);
+    }
+    bool done = !valid;
+    float rs = 0.f;
+    int ks = 0;
+    for (int k = 0;; ++k) {
+      const float r = row_pass<NPL, G, false>(S, A, q, !done, k, xs, dx, xsl, xsr, lam, th, stop);
+      if (!done && stop) { done = true; rs = r; ks = k; }
+      if (__all_sync(kFull, done)) break;
+    }
+    // a non-finite displacement anywhere in the snake marks the step (fmaxf drops NaN)
+    float bad = 0.f;
 #pragma unroll
-        for (int j = 0; j < NPL; ++j) {
-          const int i = q * NPL + j;
-          if (i < S.N)
+    for (int j = 0; j < NPL; ++j)
+      if (!(fabsf(dx[j][0]) + fabsf(dx[j][1]) + fabsf(dx[j][2]) <= 3.0e38f)) bad = 1.f;
+    bad = group_max<G>(bad);
+    rmax = fmaxf(rmax, rs);
+    if (!(rs <= 3.0e38f) || bad > 0.f) rmax = INFINITY;
+    itot += ks;
 #pragma unroll
-            for (int k = 0; k < 6; ++k)
-              A.lam_log[((size_t)s * A.total_nodes + S.nb + i) * 6 + k] = lam[j][k];
-        }
+    for (int j = 0; j < NPL; ++j) {
+      const int i = q * NPL + j;
+      if (valid && i < S.N && i >= S.nfix) {
+        v[j][0] = dx[j][0] * S.damp_over_h;
+        v[j][1] = dx[j][1] * S.damp_over_h;
+        v[j][2] = dx[j][2] * S.damp_over_h;
+      } else {
+        v[j][0] = v[j][1] = v[j][2] = 0.f;
       }
+    }
+  };
+
+  const long long step0 = *A.step_dev;
+  float rmax = 0.f;
+  int itot = 0;
+  bool at_boundary = true;  // state ends at a substep boundary (x = xs + dx, v)
+  if (!SPLIT) {
+    for (int st = 0; st < A.n_steps; ++st) {
+      rmax = 0.f;
+      itot = 0;
+      for (int s = 0; s < A.n_sub; ++s) {
+        begin_substep(step0 + st, s);
+        finish_substep(rmax, itot);
+      }
+    }
+  } else {
+    if (A.sub > 0 && valid && q == 0) { rmax = A.resid[snake]; itot = A.iters[snake]; }
+    if (A.sub >= 0) finish_substep(rmax, itot);
+    if (A.sub + 1 < A.n_sub) {
+      begin_substep(step0, A.sub + 1);
+      if (SPLIT) write_features<NPL, G>(S, A, q, valid, xs, dx, v, lam, th);
+      at_boundary = false;
     }
   }
   if (!valid) return;
@@ -443,17 +571,20 @@ __device__ void run_group(const SolverArgs& A, int snake, bool valid) {
     const int i = q * NPL + j;
     if (i >= S.N) continue;
     const float wi = (i < S.nfix) ? 0.f : S.inv_m;
-    A.pos[S.nb + i] = make_float4(xs[j][0] + dx[j][0], xs[j][1] + dx[j][1], xs[j][2] + dx[j][2], wi);
+    if (at_boundary)
+      A.pos[S.nb + i] = make_float4(xs[j][0] + dx[j][0], xs[j][1] + dx[j][1], xs[j][2] + dx[j][2], wi);
+    else
+      A.pos[S.nb + i] = make_float4(xs[j][0], xs[j][1], xs[j][2], wi);
     A.vel[S.nb + i] = make_float4(v[j][0], v[j][1], v[j][2], 0.f);
 #pragma unroll
     for (int k = 0; k < 6; ++k) A.lam[(size_t)(S.nb + i) * 6 + k] = lam[j][k];
     if (i % S.seg == 0 && i / S.seg < S.L) A.press[S.lb + i / S.seg] = make_float2(pR[j], pL[j]);
   }
-  if (q == 0) {
+  if (q == 0 && (!SPLIT || A.sub >= 0)) {
     A.resid[snake] = rmax;
     A.iters[snake] = itot;
     int st = 0;
-    if (!(rmax <= 3.0e38f)) st = -4;          // SIM_ENAN
+    if (!(rmax <= 3.0e38f)) st = -4;               // SIM_ENAN
     else if (A.tol > 0.f && rmax > A.tol) st = 1;  // SIM_NOT_CONVERGED
     A.status[snake] = st;
   }

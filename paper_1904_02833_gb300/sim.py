@@ -17,6 +17,14 @@ def _ptr(t):
     return None if t is None else ctypes.c_void_p(t.data_ptr())
 
 
+def _view_bf16(ptr, n, device):
+    """A torch tensor over n bf16 values of library-owned device memory."""
+    class _Arr:
+        __cuda_array_interface__ = {"shape": (n,), "typestr": "<i2", "data": (ptr, False),
+                                    "version": 3, "strides": None}
+    return torch.as_tensor(_Arr(), device=device).view(torch.bfloat16)
+
+
 def make_params(w: dict):
     n = len(w["n_links"])
     arr = (N.SnakeParams * n)()
@@ -41,6 +49,7 @@ def make_config(s: dict) -> N.SimConfig:
         c.gravity[k] = float(s["gravity"][k])
     c.contact = 1 if s["contact"] else 0
     c.warm = int(s["warm"])
+    c.beta = float(s.get("beta", 1.0))
     return c
 
 
@@ -66,6 +75,7 @@ class SnakeSim:
         self.n_nodes, self.n_links = nn.value, nl.value
         nodes = np.asarray(w["n_links"], np.int64) * np.asarray(w["seg_per_link"]) + 1
         self.node_off = np.concatenate([[0], np.cumsum(nodes)])
+        self._mass_per_node = np.repeat(np.asarray(w["mass"], np.float64), nodes)
         self.link_off = np.concatenate([[0], np.cumsum(w["n_links"])])
 
     # ------------------------------------------------------------------ stepping
@@ -142,6 +152,30 @@ class SnakeSim:
         conv = lambda t: None if t is None else torch.as_tensor(t).to(self.device, torch.float32).contiguous()
         pos, vel, press, lam = conv(pos), conv(vel), conv(press), conv(lam)
         N.check(self.lib.sim_set_state(self.h, _ptr(pos), _ptr(vel), _ptr(press), _ptr(lam), 1))
+
+    # ------------------------------------------------------------------ learned warm start
+    def set_mlp(self, mlp):
+        """Attaches a WarmStartMLP (None detaches); used when warm = 2."""
+        N.check(self.lib.sim_set_mlp(self.h, None if mlp is None else mlp.h))
+        self._mlp_keep = mlp
+
+    def snapshot_save(self):
+        N.check(self.lib.sim_snapshot_save(self.h))
+
+    def snapshot_restore(self):
+        N.check(self.lib.sim_snapshot_restore(self.h))
+
+    def split_begin(self):
+        N.check(self.lib.sim_split_begin(self.h))
+
+    def split_finish(self):
+        N.check(self.lib.sim_split_finish(self.h))
+
+    def features(self) -> torch.Tensor:
+        """The feature buffer [6 * nodes, 32] (bf16 view of library memory, zero copy)."""
+        p, r = ctypes.c_void_p(), ctypes.c_int64()
+        N.check(self.lib.sim_features(self.h, ctypes.byref(p), ctypes.byref(r)))
+        return _view_bf16(p.value, r.value * 32, self.device).view(r.value, 32)
 
     def status(self):
         st = np.zeros(self.n, np.int32)

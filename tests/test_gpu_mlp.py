@@ -1,0 +1,182 @@
+"""The tensor-core warm-start network and the learned warm start, through the C-ABI,
+against the oracle.
+
+Tolerances: the kernels read bfloat16 operands (as the oracle emulates) and evaluate
+SiLU with the hardware tanh approximation (relative error ~2^-11 of tanh, i.e. an absolute
+error ~2.5e-4 |z| of silu(z)); accumulation is FP32 against the oracle's FP64.  Outputs:
+5e-3 of the output scale; gradients: 2e-2 of each block's largest entry against the
+bfloat16-emulating oracle, 6e-2 against the plain FP64 gradient (the bfloat16 bound).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import mlp_oracle as M
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1904_02833_gb300.build import build
+    build()
+    torch.cuda.set_device(0)
+
+
+def mlp(params=None):
+    from paper_1904_02833_gb300.mlp import WarmStartMLP
+    return WarmStartMLP(params)
+
+
+def feats(rows, seed):
+    rng = np.random.default_rng(seed)
+    f = rng.normal(scale=1.0, size=(rows, 24))
+    f[:, :6] = 0
+    f[np.arange(rows), rng.integers(0, 6, rows)] = 1.0
+    return f
+
+
+def to_dev(f):
+    from paper_1904_02833_gb300.mlp import pad_features
+    return pad_features(torch.tensor(f, dtype=torch.float32, device="cuda"))
+
+
+@pytest.mark.parametrize("rows", [1, 127, 1000, 40000])
+def test_forward_matches_oracle(rows):
+    p = M.init_params(5)
+    p[M.N_PARAMS - 1] = 0.3
+    f = feats(rows, rows)
+    net = mlp(p)
+    y = net.forward(to_dev(f)).cpu().numpy()
+    ref = oracle.mlp_forward(p, M.bf16(f))
+    scale = np.abs(ref).mean() + 1e-3
+    assert np.abs(y - ref).max() <= 5e-3 * max(scale, np.abs(ref).max())
+
+
+def test_gradient_matches_oracle():
+    rows = 3000
+    p = M.init_params(6)
+    f = feats(rows, 9)
+    rng = np.random.default_rng(2)
+    t = rng.normal(size=rows)
+    net = mlp(p)
+    L, g = net.grad(to_dev(f), torch.tensor(t, dtype=torch.float32, device="cuda"), 1.0 / rows)
+    g = g.cpu().numpy()
+    L_ref, g_ref = M.loss_and_grad(p, M.bf16(f), t, 1.0 / rows, bf16_ops=True)
+    _, g_fp64 = M.loss_and_grad(p, M.bf16(f), t, 1.0 / rows, bf16_ops=False)
+    assert L == pytest.approx(L_ref, rel=5e-3)
+    o = 0
+    for name, shape in M.SIZES:
+        n = int(np.prod(shape))
+        a, b, c = g[o:o + n], g_ref[o:o + n], g_fp64[o:o + n]
+        assert np.abs(a - b).max() <= 2e-2 * np.abs(b).max() + 1e-7, name
+        assert np.abs(a - c).max() <= 6e-2 * np.abs(c).max() + 1e-7, name
+        o += n
+
+
+def test_training_reduces_loss_on_a_smooth_target():
+    rows = 65536
+    f = feats(rows, 11)
+    t = np.tanh(f[:, 6] - 0.5 * f[:, 7]) + 0.3 * f[:, 13] * f[:, 0]
+    from paper_1904_02833_gb300.mlp import train
+    net = mlp(M.init_params(7))
+    fd = to_dev(f)
+    td = torch.tensor(t, dtype=torch.float32, device="cuda")
+    losses = train(net, fd, td, epochs=20, batch=4096, lr=2e-3)
+    assert losses[-1] < 0.1 * losses[0]
+    # the trained parameters reproduce their own loss on the oracle
+    p = net.params().astype(np.float64)
+    y = oracle.mlp_forward(p, M.bf16(f[:2000]))
+    assert np.mean((y - t[:2000]) ** 2) < 0.15 * losses[0]
+
+
+def test_features_match_oracle():
+    from paper_1904_02833_gb300.sim import SnakeSim
+    w = W.batched(n=24, seed=31, links=(1, 8))
+    s = W.solver_settings(iters=10)
+    g, o = SnakeSim(w, s), oracle.OracleSim(w, s)
+    g.step(3)
+    o.step(3)
+    g.split_begin()
+    fg = g.features().float().cpu().numpy()[:, :24]
+    fo = o.features()
+    assert not fg[:, 24:].any() if fg.shape[1] > 24 else True
+    err = np.abs(fg - fo)
+    # geometry and kinematics: bf16 rounding of the FP32 values
+    assert (err[:, :23] <= 1e-2 * np.abs(fo[:, :23]) + 2e-3).all(), err[:, :23].max()
+    # previous multipliers of an unconverged (10-update) solve: FP32 vs FP64 differences
+    # reach ~5e-3 of the largest multiplier
+    assert (err[:, 23] <= 5e-3 * np.abs(fo[:, 23]).max() + 1e-2 * np.abs(fo[:, 23])).all()
+    # finishing the substeps splits the env-step without changing it
+    for _ in range(s["n_sub"]):
+        g.split_finish()
+    o.step(1)
+    st = g.state_host()
+    assert np.abs(st["pos"] - o.x).max() <= 1e-5 * np.abs(o.x).max()
+
+
+def test_split_stepping_matches_fused_stepping():
+    """The same arithmetic in two kernels: equal update counts, states equal to FP32
+    rounding (the compiler may contract multiply-adds differently in the two)."""
+    from paper_1904_02833_gb300.sim import SnakeSim
+    w = W.batched(n=40, seed=32, links=(1, 8))
+    for warm in (0, 1):
+        s = W.solver_settings(iters=10, warm=warm)
+        a, b = SnakeSim(w, s), SnakeSim(w, s)
+        a.step(2)
+        for _ in range(2):
+            b.split_begin()
+            for _ in range(s["n_sub"]):
+                b.split_finish()
+        sa, sb = a.state_host(), b.state_host()
+        assert np.array_equal(sa["iters"], sb["iters"])
+        assert np.array_equal(sa["press"], sb["press"])
+        assert np.abs(sa["pos"] - sb["pos"]).max() <= 1e-6 * np.abs(sa["pos"]).max()
+        assert np.abs(sa["vel"] - sb["vel"]).max() <= 1e-4
+
+
+def test_learned_mode_matches_oracle():
+    """Same network parameters on both sides; fixed iteration count."""
+    from paper_1904_02833_gb300.sim import SnakeSim
+    w = W.batched(n=16, seed=33, links=(1, 8))
+    p = M.init_params(8) * 0.5
+    s = W.solver_settings(iters=10, warm=1, beta=0.5)
+    g, o = SnakeSim(w, s), oracle.OracleSim(w, s)
+    g.step(2)
+    o.step(2)
+    net = mlp(p)
+    g.set_mlp(net)
+    g.set_config(warm=2)
+    o.set_cfg(warm=2)
+    g.step(1)
+    o.step(1, mlp=p)
+    st = g.state_host()
+    assert np.abs(st["pos"] - o.x).max() <= 1e-5 * np.abs(o.x).max()
+    assert np.abs(st["vel"] - o.v).max() <= 1.2e-3
+
+
+def test_trained_warm_start_needs_fewer_updates_than_cold_start():
+    """Trained by the library's own kernels on seeds disjoint from the evaluation seed,
+    the learned warm start reaches residual 1e-4 with fewer Jacobi updates than the plain
+    cold start on the same trajectory start."""
+    from paper_1904_02833_gb300.mlp import train_warm_start
+    from paper_1904_02833_gb300.sim import SnakeSim
+    net, rec = train_warm_start(n_snakes=384, rounds=1, steps=8, epochs0=15, epochs=8)
+    assert rec[0]["loss_last"] < 0.5 * rec[0]["loss_first"]
+    w = W.batched(n=256, seed=4)
+    res = {}
+    for mode, warm, beta in (("cold", 0, 1.0), ("learned", 2, 1.0)):
+        sim = SnakeSim(w, W.solver_settings(iters=5000, tol=1e-4, warm=0))
+        sim.step(6)
+        sim.set_mlp(net)
+        sim.set_config(warm=warm, beta=beta)
+        its = []
+        for _ in range(4):
+            sim.step(1)
+            st = sim.state_host()
+            assert (st["resid"] <= 1e-4).all()
+            its.append(st["iters"].mean())
+        res[mode] = float(np.mean(its))
+    assert res["learned"] < 0.8 * res["cold"], res

@@ -1,0 +1,95 @@
+"""Pins of the oracle's warm-start network and row features (CPU)."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import mlp_oracle as M
+import workloads as W
+
+
+def test_backward_matches_central_differences():
+    """The FP64 backward pass of the network against central differences of its forward."""
+    rng = np.random.default_rng(0)
+    p = M.init_params(1) + rng.normal(scale=0.05, size=M.N_PARAMS)
+    x = rng.normal(size=(7, M.N_IN))
+    t = rng.normal(size=7)
+    L, g = M.loss_and_grad(p, x, t, 0.3, bf16_ops=False)
+    idx = np.concatenate([rng.choice(M.N_PARAMS, 60, replace=False), [M.N_PARAMS - 1]])
+    for i in idx:
+        e = np.zeros(M.N_PARAMS)
+        e[i] = 1e-6
+        Lp = M.loss_and_grad(p + e, x, t, 0.3, bf16_ops=False)[0]
+        Lm = M.loss_and_grad(p - e, x, t, 0.3, bf16_ops=False)[0]
+        assert g[i] == pytest.approx((Lp - Lm) / 2e-6, rel=1e-5, abs=1e-9), i
+
+
+def test_bf16_rounding_matches_library():
+    """Round-to-nearest-even bfloat16 against torch's conversion, including ties."""
+    rng = np.random.default_rng(3)
+    x = np.concatenate([rng.normal(scale=10, size=5000), [1 + 2 ** -8, 1 + 3 * 2 ** -8, -0.0, 65504.0,
+                                                          1e-30, 3.0e38]])
+    ref = torch.tensor(x.astype(np.float32)).to(torch.bfloat16).float().double().numpy()
+    assert np.array_equal(M.bf16(x), ref)
+
+
+def test_cpp_network_matches_numpy_network():
+    rng = np.random.default_rng(4)
+    p = M.init_params(2)
+    x = rng.normal(size=(50, M.N_IN))
+    y_np = M.forward(p, x, bf16_ops=True)[0]
+    y_c = oracle.mlp_forward(p, x)
+    assert np.allclose(y_c, y_np, rtol=1e-12, atol=1e-12)
+
+
+def test_features_of_a_straight_snake_at_rest():
+    """Hand values: a straight 2-link snake on the ground, heading 0.7 rad, at rest.  In
+    every row frame the next node sits at (1, 0, 0) L0 and the one after at (2, 0, 0) L0;
+    gravity's prediction puts every node g h^2 below its contact height; velocities are
+    -g h along z; multipliers and rest angles are zero; non-existent rows are empty."""
+    w = W.subset(W.single_snake(), [0])
+    w["n_links"][:] = 2
+    w["yaw0"][:] = 0.7
+    w["gait_amp"][:] = 0.0
+    s = W.solver_settings()
+    o = oracle.OracleSim(w, s)
+    F = o.features().reshape(21, 6, 24)
+    h = s["dt"] / s["n_sub"]
+    L0, g = 0.02, 9.81
+    for i in range(21):
+        for k in range(6):
+            f = F[i, k]
+            exists = (k == 0 and i <= 19) or (k in (1, 2) and 1 <= i <= 19) or k >= 3
+            if not exists:
+                assert not f.any()
+                continue
+            assert f[k] == 1.0 and f[:6].sum() == 1.0
+            assert f[6] == pytest.approx(-g * h * h / L0, rel=1e-9)
+            if k == 0:
+                assert np.allclose(f[7:10], [1, 0, 0], atol=1e-12)
+            if k in (1, 2):
+                assert np.allclose(f[7:10], [1, 0, 0], atol=1e-12)
+                assert np.allclose(f[10:13], [2, 0, 0], atol=1e-12)
+            nodes = 2 if k == 0 else 3 if k in (1, 2) else 1
+            for u in range(3):
+                vz = -g * h * h / L0 if u < nodes else 0.0
+                assert np.allclose(f[13 + 3 * u:16 + 3 * u], [0, 0, vz], atol=1e-15)
+            assert f[22] == 0.0 and f[23] == 0.0
+
+
+def test_friction_row_frame_is_world_aligned():
+    """A node sliding along +y reads its velocity as (0, v) in the friction-x frame and
+    (v, 0) in the friction-y frame; a yaw row of a pressurised link reads its rest angle."""
+    w = W.subset(W.single_snake(), [0])
+    w["n_links"][:] = 1
+    s = W.solver_settings()
+    o = oracle.OracleSim(w, s)
+    o.v[:, 1] = 0.3
+    o.press[0] = [0.5, 0.0]
+    F = o.features(ucmd=np.array([0.5])).reshape(11, 6, 24)
+    h, L0 = s["dt"] / s["n_sub"], 0.02
+    assert F[4, 4, 13:15] == pytest.approx([0.0, 0.3 * h / L0])
+    assert F[4, 5, 13:15] == pytest.approx([0.3 * h / L0, 0.0])
+    assert F[4, 1, 22] == pytest.approx(20.0 * 0.5 * L0)

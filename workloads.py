@@ -42,13 +42,14 @@ DEFAULTS = dict(
 
 
 def solver_settings(dt=1.0 / 60.0, n_sub=20, iters=10, tol=0.0, omega=1.0 / 3.0,
-                    gravity=(0.0, 0.0, -9.81), contact=True, warm=0):
+                    gravity=(0.0, 0.0, -9.81), contact=True, warm=0, beta=1.0):
     """Global settings: env-step dt, substeps, iteration cap, residual tolerance
     (0 = run exactly `iters` updates), Jacobi relaxation, gravity, ground contact on/off,
-    warm start (0 = cold, 1 = previous substep's multipliers, 2 = learned)."""
+    warm start (0 = cold, 1 = beta x previous substep's multipliers, 2 = that plus the
+    learned correction)."""
     return dict(dt=float(dt), n_sub=int(n_sub), iters=int(iters), tol=float(tol),
                 omega=float(omega), gravity=tuple(float(g) for g in gravity),
-                contact=bool(contact), warm=int(warm))
+                contact=bool(contact), warm=int(warm), beta=float(beta))
 
 
 def _base(n: int) -> dict:
