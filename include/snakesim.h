@@ -222,6 +222,26 @@ SimStatus mlp_train_step(MlpHandle* m, const void* feat, const float* target, in
 SimStatus mlp_check(MlpHandle* m);
 SimStatus mlp_destroy(MlpHandle* m);
 
+/* Allocation-free forward pass, for callers that cannot allocate device memory (a
+ * control loop with a hard real-time budget that must not stall on the allocator, or a
+ * host application whose device memory belongs to its own allocator and offers this
+ * library none).  No counterpart in the paper.
+ * params: device FP32 parameter vector of n_params = MLP_NUM_PARAMS values (layout as
+ * above, owned by the caller); feat: device bf16 [rows][32]; out: device FP32 [rows];
+ * stream: cudaStream_t.  Calls no cudaMalloc / cudaFree: the bfloat16 weight copies and
+ * the timeout flag live in a fixed file-scope device array of MLP_NOALLOC_SCRATCH_BYTES
+ * bytes, held by every GPU that loads the library until the process exits.  The first
+ * call on a device, with that device current, looks up the array's device address and
+ * sets the kernel's shared-memory limit; make that first call before any stream capture
+ * begins.  The array is shared by every call on a device and keeps the
+ * last call's contents, so calls whose GPU work overlaps (other streams, other threads)
+ * race; order them on one stream.  Synchronises `stream`.  Errors: SIM_EINVAL (null
+ * pointers, rows < 0, n_params other than MLP_NUM_PARAMS -- the array holds exactly one
+ * network's weights), SIM_ECUDA. */
+#define MLP_NOALLOC_SCRATCH_BYTES 41216
+SimStatus mlp_forward_noalloc(const float* params, int32_t n_params, const void* feat,
+                              int64_t rows, float* out, void* stream);
+
 /* Attaches a network to a simulator (NULL detaches).  With warm = SIM_WARM_LEARNED every
  * substep starts from the network's multipliers; sim_step then runs each substep as
  * solver launch -> network -> solver launch (captured together by sim_step_graph).

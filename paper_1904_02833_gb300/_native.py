@@ -77,6 +77,7 @@ SIGNATURES = {
     "mlp_train_step": [H, P, P, ctypes.c_int64, ctypes.c_float, P],
     "mlp_check": [H],
     "mlp_destroy": [H],
+    "mlp_forward_noalloc": [P, ctypes.c_int32, P, ctypes.c_int64, P, P],
 }
 MLP_NUM_PARAMS = 19841
 

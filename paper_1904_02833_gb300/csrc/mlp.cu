@@ -14,6 +14,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -626,3 +627,84 @@ SimStatus mlp_destroy(MlpHandle* h) {
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------ allocation-free forward
+// Some callers cannot allocate device memory: a control loop with a hard real-time
+// budget must not stall on the CUDA allocator, and a host application that gives this
+// library a fixed device budget owned by its own allocator has no cudaMalloc to offer.
+// For them, mlp_forward_noalloc runs the network from a parameter vector they own; the
+// only working memory it needs -- the bfloat16 copies of W1 and W2 the tensor cores read,
+// and the wait-timeout flag -- lives in the file-scope array below, which every GPU that
+// loads the library holds until the process exits.
+namespace {
+constexpr size_t kNoallocW1 = (size_t)kHid * kInPad * 2;   // 8 KB
+constexpr size_t kNoallocW2 = (size_t)kHid * kHid * 2;     // 32 KB
+constexpr size_t kNoallocBytes = kNoallocW1 + kNoallocW2 + 256;  // + timeout flag
+static_assert(kNoallocBytes == MLP_NOALLOC_SCRATCH_BYTES, "documented size");
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+unsigned char* g_noalloc_addr[kMaxDevices] = {};  // device address of the array, per device
+int g_noalloc_sms[kMaxDevices] = {};
+
+// Once per device, with that device current: the array's device address (the name
+// g_noalloc_scratch in host code is only a host-side stand-in) and the kernel's
+// shared-memory opt-in.
+SimStatus noalloc_setup(int dev, unsigned char** addr, int* sms) {
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return mfail(SIM_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    e = cudaFuncSetAttribute(mlp_infer_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(InferSmem));
+    if (e != cudaSuccess) return mfail(SIM_ECUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e));
+    int n = 0;
+    e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return mfail(SIM_ECUDA, std::string("cudaDeviceGetAttribute: ") + cudaGetErrorString(e));
+    g_noalloc_sms[dev] = n;
+    g_noalloc_addr[dev] = static_cast<unsigned char*>(p);
+  }
+  *addr = g_noalloc_addr[dev];
+  *sms = g_noalloc_sms[dev];
+  return SIM_OK;
+}
+}  // namespace
+
+extern "C" SimStatus mlp_forward_noalloc(const float* params, int32_t n_params, const void* feat,
+                                         int64_t rows, float* out, void* stream) {
+  if (!params || !feat || !out || rows < 0) return mfail(SIM_EINVAL, "null pointer or rows < 0");
+  if (n_params != kNumParams)
+    return mfail(SIM_EINVAL, "mlp_forward_noalloc: its static working array holds the bfloat16 weights of "
+                             "exactly one 24-128-128-1 network (" + std::to_string(kNumParams) +
+                             " parameters, " + std::to_string(kNoallocBytes) + " bytes); got " +
+                             std::to_string(n_params) + " parameters");
+  int dev = 0;
+  MCU(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return mfail(SIM_EINVAL, "device index out of range");
+  unsigned char* base = nullptr;
+  int sms = 0;
+  SimStatus s = noalloc_setup(dev, &base, &sms);
+  if (s != SIM_OK) return s;
+  if (rows == 0) return SIM_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  __nv_bfloat16* w1b = reinterpret_cast<__nv_bfloat16*>(base);
+  __nv_bfloat16* w2b = reinterpret_cast<__nv_bfloat16*>(base + kNoallocW1);
+  int* err = reinterpret_cast<int*>(base + kNoallocW1 + kNoallocW2);
+  // the array keeps the previous call's contents: the flag must start at zero
+  MCU(cudaMemsetAsync(err, 0, sizeof(int), st));
+  mlp_pack_kernel<<<(kHid * kHid + 255) / 256, 256, 0, st>>>(params, w1b, w2b);
+  MCU(cudaGetLastError());
+  MlpDev d;
+  d.w1 = w1b; d.w2 = w2b;
+  d.b1 = params + kOffB1; d.b2 = params + kOffB2; d.w3 = params + kOffW3; d.b3 = params + kOffB3;
+  const long long tiles = (rows + kTile - 1) / kTile;
+  const int grid = (int)std::min<long long>(tiles, 2LL * sms);
+  mlp_infer_kernel<<<grid, 128, sizeof(InferSmem), st>>>((const __nv_bfloat16*)feat, rows, d, out, err);
+  MCU(cudaGetLastError());
+  int e = 0;
+  MCU(cudaMemcpyAsync(&e, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  MCU(cudaStreamSynchronize(st));
+  if (e) return mfail(SIM_ECUDA, "tensor-core wait timed out");
+  return SIM_OK;
+}
