@@ -127,7 +127,13 @@ def run_gpu(args):
 
     # untimed set-up: the warm-start network is trained on solver data (training seeds)
     t_train = time.perf_counter()
-    net, record = train_warm_start(n_snakes=1024, rounds=2)
+    if args.load_net:
+        from paper_1904_02833_gb300.mlp import WarmStartMLP
+        net, record = WarmStartMLP(np.load(args.load_net)), [{"loaded": args.load_net}]
+    else:
+        net, record = train_warm_start(n_snakes=1024, rounds=2)
+    if args.save_net:
+        np.save(args.save_net, net.params())
     t_train = time.perf_counter() - t_train
 
     w = W.learned(n=N_SNAKES, seed=4)  # evaluation batch (seed disjoint from training)
@@ -366,6 +372,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--save-net", default=None, help="write the trained network parameters (.npy)")
+    ap.add_argument("--load-net", default=None, help="use saved network parameters instead of training")
     ap.add_argument("--snakes", type=int, default=N_SNAKES,
                     help="batch size per GPU (smaller batches for profiler captures)")
     args = ap.parse_args()

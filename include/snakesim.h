@@ -183,6 +183,28 @@ SimStatus sim_step_graph(SimHandle* h, int n_steps);
 SimStatus sim_snapshot_save(SimHandle* h);
 SimStatus sim_snapshot_restore(SimHandle* h);
 
+/* ---------------------------------------------------------------- calibration adjoint
+ * Gradients for calibrating five per-snake parameters theta = (alpha_b, damping d,
+ * tau_inflate, tau_deflate, gain G) against observed trajectories (no counterpart in the
+ * paper, which tunes its latency gains by hand, Sec. VI-B).
+ *
+ * sim_calib_forward runs n_steps env-steps from the current state with theta (device
+ * FP32 [n_snakes][5]) replacing those parameters, every substep starting cold and
+ * applying exactly `iters` Jacobi updates (the configuration's tol and warm start are
+ * not used; the gait of Eq. 9 drives the links, a command override is ignored).  It
+ * writes the last node's position after every env-step to tips (device FP32
+ * [n_steps][n_snakes][3]), keeps the state every ckpt_every env-steps as a checkpoint,
+ * and advances the simulator.
+ * sim_calib_backward takes d L / d tips (device [n_steps][n_snakes][3]) and writes
+ * d L / d theta (device [n_snakes][5]) for the executed discrete map: each checkpoint
+ * segment is recomputed, its substeps are walked in reverse and, inside each, the K
+ * iterates are recomputed and transposed (clamps and the friction projection take the
+ * derivative of the branch they took).  Working memory grows with ckpt_every x n_sub
+ * substep states per snake.  Errors: SIM_EINVAL, SIM_ENOMEM, SIM_ECUDA. */
+SimStatus sim_calib_forward(SimHandle* h, const float* theta, int n_steps, int ckpt_every,
+                            float* tips);
+SimStatus sim_calib_backward(SimHandle* h, const float* tips_bar, float* grad_theta);
+
 /* Kernel launches made by this handle so far (the count the benchmark reports). */
 SimStatus sim_launch_count(SimHandle* h, int64_t* launches);
 

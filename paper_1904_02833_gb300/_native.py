@@ -65,6 +65,8 @@ SIGNATURES = {
     "sim_destroy": [H],
     "sim_set_mlp": [H, H],
     "sim_snapshot_save": [H],
+    "sim_calib_forward": [H, P, ctypes.c_int, ctypes.c_int, P],
+    "sim_calib_backward": [H, P, P],
     "sim_snapshot_restore": [H],
     "sim_split_begin": [H],
     "sim_split_finish": [H],

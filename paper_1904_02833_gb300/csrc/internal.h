@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 #include "snakesim.h"
 
 namespace snakesim {
@@ -48,6 +50,18 @@ struct SolverArgs {
   int warm;
   float beta;
 };
+
+// Calibration (adjoint) state of a simulator, defined in adjoint.cu.
+struct CalibState;
+CalibState* calib_new();
+void calib_delete(CalibState* c);
+SimStatus calib_forward(CalibState& C, const SnakeParams* prm, const int* node_off, const int* link_off,
+                        int n_snakes, int n_max, int l_max, const float* theta, int n_steps, int ckpt,
+                        long long step0, int n_sub, int K, int contact, double dt, float omega,
+                        const float* gvec, float4* pos4, float4* vel4, float2* press2, float* tips,
+                        cudaStream_t st, std::string& err);
+SimStatus calib_backward(CalibState& C, const SnakeParams* prm, const int* node_off, const int* link_off,
+                         const float* tips_bar, float* grad, cudaStream_t st, std::string& err);
 
 // Records the message returned by sim_last_error() on this thread.
 void set_last_error(const char* msg);

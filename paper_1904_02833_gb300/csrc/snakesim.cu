@@ -126,6 +126,8 @@ struct SimHandle {
   float* lam0 = nullptr;            // network output, normalised multipliers [nodes][6]
   __nv_bfloat16* feat = nullptr;   // features [nodes * 6][32]
   MlpHandle* mlp = nullptr;
+  CalibState* calib = nullptr;
+  int max_nodes = 0, max_links = 0;
   int cur_sub = -1;                // split stepping: substep begun, -1 at a step boundary
   // snapshot
   float4 *snap_pos = nullptr, *snap_vel = nullptr;
@@ -358,6 +360,10 @@ SimStatus sim_create(const SimConfig* cfg, int n_snakes, const SnakeParams* para
   }
   h->n_nodes = h->node_off[n_snakes];
   h->n_links = h->link_off[n_snakes];
+  for (int s = 0; s < n_snakes; ++s) {
+    h->max_nodes = std::max(h->max_nodes, h->node_off[s + 1] - h->node_off[s]);
+    h->max_links = std::max(h->max_links, h->link_off[s + 1] - h->link_off[s]);
+  }
   auto cleanup = [&](SimStatus s) { sim_destroy(h); return s; };
   // host-side initial pose: straight along yaw0 from (x0, y0, z0), at rest
   std::vector<float4> pos(h->n_nodes), vel(h->n_nodes, make_float4(0.f, 0.f, 0.f, 0.f));
@@ -761,6 +767,34 @@ SimStatus sim_snapshot_restore(SimHandle* h) {
   return SIM_OK;
 }
 
+SimStatus sim_calib_forward(SimHandle* h, const float* theta, int n_steps, int ckpt_every, float* tips) {
+  if (!h || !theta || !tips) return fail(SIM_EINVAL, "null handle or buffer");
+  if (n_steps < 1 || ckpt_every < 1) return fail(SIM_EINVAL, "n_steps and ckpt_every must be >= 1");
+  if (h->cur_sub >= 0) return fail(SIM_EINVAL, "a split env-step is in progress (sim_split_finish)");
+  if (!h->calib) h->calib = calib_new();
+  std::string err;
+  SimStatus st = calib_forward(*h->calib, h->prm, h->node_off_d, h->link_off_d, h->n, h->max_nodes,
+                               h->max_links, theta, n_steps, ckpt_every, h->step_index, h->cfg.n_sub,
+                               h->cfg.iters, h->cfg.contact, h->cfg.dt, h->cfg.omega, h->cfg.gravity,
+                               h->pos, h->vel, h->press, tips, h->stream, err);
+  if (st != SIM_OK) return fail(st, err);
+  st = advance(h, n_steps, h->stream);
+  if (st != SIM_OK) return st;
+  h->step_index += n_steps;
+  h->launches += 2 + (n_steps + ckpt_every - 1) / ckpt_every;
+  return SIM_OK;
+}
+
+SimStatus sim_calib_backward(SimHandle* h, const float* tips_bar, float* grad_theta) {
+  if (!h || !tips_bar || !grad_theta) return fail(SIM_EINVAL, "null handle or buffer");
+  if (!h->calib) return fail(SIM_EINVAL, "no calibration forward pass to differentiate");
+  std::string err;
+  SimStatus st = calib_backward(*h->calib, h->prm, h->node_off_d, h->link_off_d, tips_bar, grad_theta,
+                                h->stream, err);
+  if (st != SIM_OK) return fail(st, err);
+  return SIM_OK;
+}
+
 SimStatus sim_launch_count(SimHandle* h, int64_t* launches) {
   if (!h || !launches) return fail(SIM_EINVAL, "null handle or output");
   *launches = h->launches;
@@ -771,6 +805,7 @@ SimStatus sim_destroy(SimHandle* h) {
   if (!h) return SIM_OK;
   cudaStreamSynchronize(h->stream);
   if (h->graph) cudaGraphExecDestroy(h->graph);
+  if (h->calib) calib_delete(h->calib);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
   if (h->ev_join) cudaEventDestroy(h->ev_join);
