@@ -31,6 +31,7 @@ METRIC = "snake env-steps/s at residual<=1e-4, learned warm-start vs plain, 1 GB
 N_SNAKES = 16384
 TOL = 1e-4
 CAP = 5000
+SKIP = 0.5  # learned warm start: lambda0 = SKIP lambda_prev + m g h^2 network(features)
 # Algorithmic FP32 operations of one Jacobi pass per node (segment geometry 29, stretch
 # 23, yaw 46, pitch 52, contact + friction 54, update 12; a division, square root or
 # transcendental counts as one operation).
@@ -131,7 +132,7 @@ def run_gpu(args):
         from paper_1904_02833_gb300.mlp import WarmStartMLP
         net, record = WarmStartMLP(np.load(args.load_net)), [{"loaded": args.load_net}]
     else:
-        net, record = train_warm_start(n_snakes=1024, rounds=2)
+        net, record = train_warm_start(n_snakes=1024, rounds=2, skip=SKIP)
     if args.save_net:
         np.save(args.save_net, net.params())
     t_train = time.perf_counter() - t_train
@@ -151,7 +152,7 @@ def run_gpu(args):
     sim.snapshot_save()
 
     modes = [("plain", dict(warm=0, beta=1.0)), ("previous", dict(warm=1, beta=0.5)),
-             ("learned", dict(warm=2, beta=1.0))]
+             ("learned", dict(warm=2, beta=SKIP))]
     results = {}
     clk_all = None
     for name, cfg in modes:
@@ -210,7 +211,7 @@ def run_gpu(args):
 
     # end to end, learned mode, through the public API with the state in pinned host
     # memory: the same K env-steps from the same start, state copied in and out each step
-    sim.set_config(warm=2, beta=1.0)
+    sim.set_config(warm=2, beta=SKIP)
     sim.snapshot_restore()
     start = sim.state()
     start_lam = sim.lam()

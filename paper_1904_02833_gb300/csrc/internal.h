@@ -31,6 +31,7 @@ struct SolverArgs {
   const int4* items;      // [n_items] (offset into order, snakes in item, layout id, 0)
   const int* order;       // snake indices grouped by layout
   int n_items;
+  int* work;              // work-queue counter of this launch (zeroed before the launch)
   const float* ucmd;      // [links] command override or null
   const float* lam0;      // learned warm start, normalised multipliers [nodes][6] or null
   __nv_bfloat16* feat;    // warm-start features [nodes * 6][32] (split mode)

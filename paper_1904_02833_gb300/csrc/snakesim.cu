@@ -52,12 +52,16 @@ namespace {
 #ifndef SNAKE_MIN_BLOCKS
 #define SNAKE_MIN_BLOCKS 3
 #endif
+// Persistent: every warp takes the next work item (32/G snakes of one length) from a
+// counter in global memory until none is left; items are ordered longest first.
 template <int NPL, bool SPLIT>
 __global__ void __launch_bounds__(128, SNAKE_MIN_BLOCKS) snake_solver_kernel(SolverArgs A) {
-  const int warp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-  const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
   const int lane = threadIdx.x & 31;
-  for (int it = warp; it < A.n_items; it += nwarps) {
+  for (;;) {
+    int it = 0;
+    if (lane == 0) it = atomicAdd(A.work, 1);
+    it = __shfl_sync(0xffffffffu, it, 0);
+    if (it >= A.n_items) break;
     const int4 item = A.items[it];
     const int G = layout_lanes(item.z);
     const int gi = lane / G;
@@ -117,6 +121,7 @@ struct SimHandle {
   int n_items = 0;
   int npl_first[5] = {0, 0, 0, 0, 0};  // items of nodes-per-lane p are [first[p-1], first[p])
   int npl_grid[4] = {0, 0, 0, 0};
+  int* work = nullptr;  // [4] work-queue counters, one per solver kernel
   cudaStream_t side[4] = {nullptr, nullptr, nullptr, nullptr};
   cudaEvent_t ev_side[4] = {nullptr, nullptr, nullptr, nullptr};
   float* ucmd = nullptr;
@@ -188,14 +193,15 @@ SimStatus build_items(SimHandle* h, const std::map<int, int>* only_bucket = null
       it.off = (int)order.size();
       it.cnt = (int)std::min<size_t>(per, kv.second.size() - b);
       it.lay = lay;
-      it.cost = (float)layout_npl(lay);
+      it.cost = (float)kv.first;  // node count: longer snakes take longer
       for (int c = 0; c < it.cnt; ++c) order.push_back(kv.second[b + c]);
       its.push_back(it);
     }
   }
-  // items ordered by nodes per lane (one kernel each), then by snake length inside
+  // items ordered by nodes per lane (one kernel each), longest snakes first inside
   std::stable_sort(its.begin(), its.end(), [](const It& a, const It& b) {
-    return layout_npl(a.lay) < layout_npl(b.lay);
+    if (layout_npl(a.lay) != layout_npl(b.lay)) return layout_npl(a.lay) < layout_npl(b.lay);
+    return a.cost > b.cost;
   });
   std::vector<int4> hitems(its.size());
   for (size_t i = 0; i < its.size(); ++i) hitems[i] = make_int4(its[i].off, its[i].cnt, its[i].lay, 0);
@@ -310,8 +316,10 @@ SimStatus launch_args(SimHandle* h, const SolverArgs& A, cudaStream_t st) {
     SolverArgs B = A;
     B.items = h->items + h->npl_first[p];
     B.n_items = h->npl_first[p + 1] - h->npl_first[p];
+    B.work = h->work + p;
     cudaStream_t s = fork ? h->side[p] : st;
     if (fork) CU(cudaStreamWaitEvent(s, h->ev_fork, 0));
+    CU(cudaMemsetAsync(B.work, 0, sizeof(int), s));
     kSolverKernels[A.split ? 1 : 0][p]<<<h->npl_grid[p], 128, 0, s>>>(B);
     CU(cudaGetLastError());
     h->launches += 1;
@@ -397,6 +405,7 @@ SimStatus sim_create(const SimConfig* cfg, int n_snakes, const SnakeParams* para
   ALLOC(h->scratch3, h->n_nodes * 6 * sizeof(float));
   ALLOC(h->lam0, h->n_nodes * 6 * sizeof(float));
   ALLOC(h->step_dev, sizeof(long long));
+  ALLOC(h->work, 4 * sizeof(int));
   ALLOC(h->feat, h->n_nodes * 6 * 32 * sizeof(__nv_bfloat16));
 #undef ALLOC
 #define CUC(call)                                                                         \
@@ -816,7 +825,7 @@ SimStatus sim_destroy(SimHandle* h) {
   void* ptrs[] = {h->pos, h->vel, h->press, h->lam, h->prm, h->node_off_d, h->link_off_d, h->resid,
                   h->iters, h->status, h->items, h->order, h->ucmd, h->inv_mass_d, h->scratch3,
                   h->lam0, h->feat, h->snap_pos, h->snap_vel, h->snap_press, h->snap_lam,
-                  h->step_dev, h->snap_step_dev};
+                  h->step_dev, h->snap_step_dev, h->work};
   for (void* p : ptrs) if (p) cudaFree(p);
   delete h;
   return SIM_OK;

@@ -37,6 +37,35 @@ namespace snakesim {
 
 constexpr unsigned kFull = 0xffffffffu;
 
+// atan(t) on [-1, 1]: odd polynomial t P(t^2) of degree 8 in t^2, a near-minimax fit
+// (iteratively reweighted least squares on Chebyshev nodes) made for this library; its
+// FP32 evaluation stays within ~1.1e-7 of atan (tests/test_fast_atan.py).  Beyond
+// |t| = 1, atan(t) = sign(t) pi/2 - atan(1/t).
+__device__ __forceinline__ float atan_unit(float t) {
+  const float s = t * t;
+  float p = 2.456724454e-03f;
+  p = fmaf(p, s, -1.440136063e-02f);
+  p = fmaf(p, s, 3.978123527e-02f);
+  p = fmaf(p, s, -7.234859260e-02f);
+  p = fmaf(p, s, 1.049894763e-01f);
+  p = fmaf(p, s, -1.416122988e-01f);
+  p = fmaf(p, s, 1.998590693e-01f);
+  p = fmaf(p, s, -3.333259705e-01f);
+  p = fmaf(p, s, 9.999998864e-01f);
+  return t * p;
+}
+__device__ __forceinline__ float atan_any(float t) {
+  const float a = fabsf(t);
+  if (a <= 1.f) return atan_unit(t);
+  return copysignf(1.57079632679489662f - atan_unit(__frcp_rn(a)), t);
+}
+// atan2(y, x) for the bend angles: x > 0 (|angle| < 90 degrees, the normal case) takes the
+// polynomial; anything else falls back to atan2f.
+__device__ __forceinline__ float atan2_bend(float y, float x) {
+  if (x > 0.f) return atan_any(__fdividef(y, x));
+  return atan2f(y, x);
+}
+
 struct Seg {  // derived quantities of the segment from node i to node i+1
   float ex, ey, ez;   // edge vector
   float len;          // |e|
@@ -54,15 +83,15 @@ __device__ __forceinline__ Seg make_seg(float ex, float ey, float ez, float L0) 
   const float il = rsqrtf(l2);
   s.len = l2 * il;
   s.nx = s.ex * il; s.ny = s.ey * il; s.nz = s.ez * il;
-  const float ih2 = 1.0f / h2;
   const float ih = rsqrtf(h2);
+  const float ih2 = ih * ih;
   s.gyx = -L0 * s.ey * ih2;
   s.gyy = L0 * s.ex * ih2;
   const float f = L0 * il * il * ih;
   s.gpx = -s.ez * s.ex * f;
   s.gpy = -s.ez * s.ey * f;
   s.gpz = h2 * f;
-  s.beta = atan2f(s.ez, h2 * ih);
+  s.beta = atan_any(s.ez * ih);  // atan2(e_z, |e_h|), |e_h| > 0
   return s;
 }
 
@@ -109,7 +138,7 @@ __device__ __forceinline__ float row_pass(const SnakeK& S, const SolverArgs& A, 
 #pragma unroll
     for (int k = 0; k < 6; ++k) dl[j][k] = 0.f;
   }
-  float r = 0.f;
+  float r = 0.f, q2 = 0.f;
   const int i0 = q * NPL;
   // segment i0-1 (from the left neighbour's last node to my first node)
   Seg sp;
@@ -152,7 +181,7 @@ __device__ __forceinline__ float row_pass(const SnakeK& S, const SolverArgs& A, 
         if (WARM) d = lam[j][0];
         else {
           r = fmaxf(r, fabsf(c + S.at_s * l) * S.inv_L0);
-          d = A.omega * (-c - S.at_s * l) / (wg + S.at_s);
+          d = __fdividef(A.omega * (-c - S.at_s * l), wg + S.at_s);
         }
         dl[j][0] = d;
         acc[j][0] -= sc.nx * d; acc[j][1] -= sc.ny * d; acc[j][2] -= sc.nz * d;
@@ -165,7 +194,7 @@ __device__ __forceinline__ float row_pass(const SnakeK& S, const SolverArgs& A, 
       {
         const float cz = sp.ex * sc.ey - sp.ey * sc.ex;
         const float dh = sp.ex * sc.ex + sp.ey * sc.ey;
-        const float c = L0 * (atan2f(cz, dh) - th[j]);
+        const float c = L0 * (atan2_bend(cz, dh) - th[j]);
         const float g0x = sp.gyx, g0y = sp.gyy;                   // node i-1
         const float g1x = -sp.gyx - sc.gyx, g1y = -sp.gyy - sc.gyy; // node i
         const float g2x = sc.gyx, g2y = sc.gyy;                   // node i+1
@@ -177,7 +206,7 @@ __device__ __forceinline__ float row_pass(const SnakeK& S, const SolverArgs& A, 
           else {
             const float l = lam[j][1];
             r = fmaxf(r, fabsf(c + S.at_b * l) * S.inv_L0);
-            d = A.omega * (-c - S.at_b * l) / (wg + S.at_b);
+            d = __fdividef(A.omega * (-c - S.at_b * l), wg + S.at_b);
           }
           dl[j][1] = d;
           tl[0] += g0x * d; tl[1] += g0y * d;
@@ -200,7 +229,7 @@ __device__ __forceinline__ float row_pass(const SnakeK& S, const SolverArgs& A, 
           else {
             const float l = lam[j][2];
             r = fmaxf(r, fabsf(c + S.at_b * l) * S.inv_L0);
-            d = A.omega * (-c - S.at_b * l) / (wg + S.at_b);
+            d = __fdividef(A.omega * (-c - S.at_b * l), wg + S.at_b);
           }
           dl[j][2] = d;
           tl[0] += g0x * d; tl[1] += g0y * d; tl[2] += g0z * d;
@@ -223,11 +252,13 @@ __device__ __forceinline__ float row_pass(const SnakeK& S, const SolverArgs& A, 
         const float rho = wi * S.mu * ln;
         const float ax = wi * lam[j][4], ay = wi * lam[j][5];
         float px = ax - ux, py = ay - uy;
-        const float pn = sqrtf(px * px + py * py);
-        if (pn > rho) {
-          if (rho > 0.f) { px *= rho / pn; py *= rho / pn; } else { px = 0.f; py = 0.f; }
+        const float pn2 = px * px + py * py;
+        if (pn2 > rho * rho) {
+          if (rho > 0.f) { const float sc1 = rho * rsqrtf(pn2); px *= sc1; py *= sc1; }
+          else { px = 0.f; py = 0.f; }
         }
-        r = fmaxf(r, sqrtf((ax - px) * (ax - px) + (ay - py) * (ay - py)) * S.inv_L0);
+        // squared friction residual; one square root per pass for the whole lane
+        q2 = fmaxf(q2, (ax - px) * (ax - px) + (ay - py) * (ay - py));
         // contact: lambda_n <- max(0, lambda_n + omega (-c_n / w))
         const float nl = fmaxf(0.f, ln - A.omega * cn * S.mass);
         dn = nl - ln;
@@ -239,7 +270,7 @@ __device__ __forceinline__ float row_pass(const SnakeK& S, const SolverArgs& A, 
         const float n2 = tx * tx + ty * ty;
         if (n2 > rad * rad) {
           if (rad <= 0.f) { tx = 0.f; ty = 0.f; }
-          else { const float sc2 = rad / sqrtf(n2); tx *= sc2; ty *= sc2; }
+          else { const float sc2 = rad * rsqrtf(n2); tx *= sc2; ty *= sc2; }
         }
         dx = tx - lam[j][4]; dy = ty - lam[j][5];
       }
@@ -251,6 +282,7 @@ __device__ __forceinline__ float row_pass(const SnakeK& S, const SolverArgs& A, 
     sp = sc;
   }
   if (!WARM) {
+    r = fmaxf(r, sqrtf(q2) * S.inv_L0);
     if (!(r <= 3.0e38f)) r = INFINITY;  // NaN -> inf so that the max keeps it
     r = group_max<G>(r);
     stop = (r <= A.tol) || (kiter >= A.K);

@@ -155,16 +155,17 @@ def train(mlp: WarmStartMLP, feat, target, epochs: int = 10, batch: int = 16384,
 
 def train_warm_start(n_snakes: int = 1024, seeds=None, rounds: int = 2, settle: int = 6,
                      steps: int = 10, tol: float = 1e-4, epochs0: int = 20, epochs: int = 10,
-                     batch: int = 16384, log=None, make_batch=None):
+                     batch: int = 16384, log=None, make_batch=None, skip: float = 0.5):
     """Trains the warm-start network on data the plain solver generates.
 
     Round 0 follows cold-start trajectories; every later round follows trajectories of
     the learned warm start itself (on new seeds), so the network sees the previous
     multipliers it will meet when deployed.  Targets: at a logged substep, the
     multipliers the plain cold-start solver reaches at `tol` from the same start,
-    minus the previous multipliers (the learned warm start adds the network's output to
-    the previous multipliers, weight 1).  All simulation and all training run in the
-    library's kernels.  Returns the network and a record of the rounds."""
+    minus `skip` times the previous multipliers (the learned warm start adds the network's
+    output to the previous multipliers weighted by beta = skip).  All simulation and all
+    training run in the library's kernels.  Returns the network and a record of the
+    rounds."""
     import workloads as W  # seeded parameter generator (no simulation arithmetic)
     from .sim import SnakeSim
 
@@ -178,9 +179,9 @@ def train_warm_start(n_snakes: int = 1024, seeds=None, rounds: int = 2, settle: 
         sim.step(settle)
         if learned:
             sim.set_mlp(net)
-            sim.set_config(warm=2, beta=1.0)
+            sim.set_config(warm=2, beta=skip)
             sim.step(2)
-        f, t = collect(sim, steps, substeps=(0, 7, 14), every=2, target_tol=tol, skip=1.0)
+        f, t = collect(sim, steps, substeps=(0, 7, 14), every=2, target_tol=tol, skip=skip)
         sim.close()
         return f, t
 
