@@ -44,6 +44,23 @@ BYTES_PER_LINK = 16
 BYTES_PER_SNAKE = 116
 
 
+def shard_seed(rank: int) -> int:
+    """Evaluation batch of a rank: rank 0 runs the evaluation seed 4, other ranks their own
+    seeds (independent snakes, weak scaling); all below the training seeds (1000+)."""
+    return 4 if rank == 0 else 100 + rank
+
+
+def aggregate(t_local: float, units_local: int, dist=None, device="cpu"):
+    """Whole-job throughput: the slowest rank's time and the units all ranks processed."""
+    import torch
+    t = torch.tensor([t_local], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units_local)], dtype=torch.float64, device=device)
+    if dist is not None and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(u.item()) / float(t.item()), float(t.item()), float(u.item())
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -137,7 +154,7 @@ def run_gpu(args):
         np.save(args.save_net, net.params())
     t_train = time.perf_counter() - t_train
 
-    w = W.learned(n=N_SNAKES, seed=4)  # evaluation batch (seed disjoint from training)
+    w = W.learned(n=N_SNAKES, seed=shard_seed(rank))  # disjoint from the training seeds
     n_nodes_snake = w["n_links"] * w["seg_per_link"] + 1
     total_nodes = int(n_nodes_snake.sum())
     total_links = int(w["n_links"].sum())
@@ -183,10 +200,8 @@ def run_gpu(args):
             barrier()
         ms = [a.elapsed_time(b) for a, b in ev]
         t_local = sum(ms) / 1e3
-        t = torch.tensor([t_local], dtype=torch.float64, device="cuda")
-        if world > 1:
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        results[name] = dict(t=float(t.item()), t_local=t_local, passes=passes, resid_max=resid_max,
+        value_all, t_max, _ = aggregate(t_local, N_SNAKES * args.steps, dist, "cuda")
+        results[name] = dict(t=t_max, value=value_all, t_local=t_local, passes=passes, resid_max=resid_max,
                              unconverged=unconv, updates=upd, launches=sim.launches() - l0,
                              clocks=clk.summary())
         if name == "learned":
@@ -230,16 +245,14 @@ def run_gpu(args):
             host[k].copy_(d[k], non_blocking=True)
     torch.cuda.synchronize()
     t_e2e = time.perf_counter() - t0
-    te = torch.tensor([t_e2e], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_value, _, _ = aggregate(t_e2e, N_SNAKES * args.steps, dist, "cuda")
     h2d = int(sum(host[k].numel() * host[k].element_size() for k in inputs))
     d2h = int(sum(v.numel() * v.element_size() for v in host.values()))
 
     if rank == 0:
         pk = peaks()
         L = results["learned"]
-        value = N_SNAKES * args.steps * world / L["t"]
+        value = L["value"]
         alu_peak = 152 * 128 * 2 * 2070.0 * 1e6 / 1e12
         # solver family in the learned mode: Jacobi passes per step x 216 FLOP / time
         # (the network's share of the step is taken out with its own measured time)
@@ -254,7 +267,7 @@ def run_gpu(args):
         for name, _ in modes:
             R = results[name]
             modes_out[name] = {
-                "value": N_SNAKES * args.steps * world / R["t"], "ms_per_step": R["t"] * 1e3 / args.steps,
+                "value": R["value"], "ms_per_step": R["t"] * 1e3 / args.steps,
                 "updates_per_substep_by_step": [round(u, 2) for u in R["updates"]],
                 "residual_max": R["resid_max"], "unconverged_snake_steps": R["unconverged"],
                 "gpu_launches": R["launches"], "clocks": R["clocks"]}
@@ -292,7 +305,7 @@ def run_gpu(args):
                                  "unit": "TFLOP/s", "frac": mlp_tflops / bf16_peak,
                                  "ms_per_launch": mlp_ms, "rows": rows,
                                  "peak_source": "MEASURED_PEAKS bf16_tflops (burst, of measured)"}},
-            "e2e": {"value": N_SNAKES * args.steps * world / float(te.item()), "unit": "env-steps/s",
+            "e2e": {"value": e2e_value, "unit": "env-steps/s",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": int(L["launches"]),
             "clocks": clk_all.summary() if clk_all else None,

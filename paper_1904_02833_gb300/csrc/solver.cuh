@@ -284,8 +284,13 @@ __device__ __forceinline__ float row_pass(const SnakeK& S, const SolverArgs& A, 
   if (!WARM) {
     r = fmaxf(r, sqrtf(q2) * S.inv_L0);
     if (!(r <= 3.0e38f)) r = INFINITY;  // NaN -> inf so that the max keeps it
-    r = group_max<G>(r);
-    stop = (r <= A.tol) || (kiter >= A.K);
+    // one ballot decides every group's stop; the group's max residual is reduced only in
+    // the (rare) passes where some live group stops, to be recorded
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned over = __ballot_sync(kFull, !(r <= A.tol));
+    const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(unsigned)(G - 1)));
+    stop = ((over & gmask) == 0u) || (kiter >= A.K);
+    if (__any_sync(kFull, stop && live)) r = group_max<G>(r);
   } else {
     stop = false;
   }
