@@ -81,6 +81,70 @@ const SolverKernel kSolverKernels[2][4] = {
     {snake_solver_kernel<1, true>, snake_solver_kernel<2, true>, snake_solver_kernel<3, true>,
      snake_solver_kernel<4, true>}};
 
+// ------------------------------------------------------------------ scheduling
+// Before every env-step the snakes of each node-count class are ranked on the device by
+// the Jacobi updates they needed in the previous env-step (temporal coherence), and
+// consecutive snakes of the ranking share a warp: the lane groups of a warp run in lock
+// step until the slowest one has converged, so grouping snakes of similar cost wastes
+// fewer passes, and each class's items are then queued most expensive first.  (Queueing
+// all items in one most-expensive-first order measured slower than keeping the classes
+// in their static order.)  The physics of a snake does not depend on the warp it gets.
+struct SchedArgs {
+  const int* iters;     // [S] updates of the previous env-step (0: none yet)
+  const int* node_off;  // [S + 1]
+  const int* cls;       // [S] class of each snake (-1: not scheduled)
+  const int* cls_base;  // [C] first slot of the class in `order`
+  int* hist;            // [C * 256] scratch
+  int* order;           // out: the snakes of class c at [cls_base[c], cls_base[c] + count)
+  int n, n_cls;
+};
+
+// Cost bin of a snake, 16 bins per octave of its update count (its node count before the
+// first step); bins count down so that the expensive snakes come first.
+__device__ __forceinline__ int sched_bin(const SchedArgs& a, int s) {
+  int v = a.iters[s];
+  if (v <= 0) v = a.node_off[s + 1] - a.node_off[s];
+  v = max(v, 1);
+  const int e = 31 - __clz(v);
+  const int m = e >= 4 ? (v >> (e - 4)) & 15 : (v << (4 - e)) & 15;
+  return 255 - min(255, 16 * e + m);
+}
+
+// In-place exclusive prefix sum of 256 counters by one warp.
+__device__ __forceinline__ void warp_scan256(int* c) {
+  const int lane = threadIdx.x & 31;
+  int v[8], sum = 0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) { v[k] = c[lane * 8 + k]; sum += v[k]; }
+  int inc = sum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int t = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += t;
+  }
+  int run = inc - sum;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) { c[lane * 8 + k] = run; run += v[k]; }
+}
+
+// One block: counting sort of the snakes by (class, cost bin).
+__global__ void __launch_bounds__(1024) schedule_kernel(SchedArgs a) {
+  const int t = threadIdx.x, T = blockDim.x, warp = t >> 5, nw = T >> 5;
+  for (int i = t; i < a.n_cls * 256; i += T) a.hist[i] = 0;
+  __syncthreads();
+  for (int s = t; s < a.n; s += T) {
+    const int c = a.cls[s];
+    if (c >= 0) atomicAdd(&a.hist[c * 256 + sched_bin(a, s)], 1);
+  }
+  __syncthreads();
+  for (int r = warp; r < a.n_cls; r += nw) warp_scan256(a.hist + r * 256);
+  __syncthreads();
+  for (int s = t; s < a.n; s += T) {
+    const int c = a.cls[s];
+    if (c >= 0) a.order[a.cls_base[c] + atomicAdd(&a.hist[c * 256 + sched_bin(a, s)], 1)] = s;
+  }
+}
+
 // Advances the device env-step counter once all solver launches of a step are done.
 __global__ void advance_step_kernel(long long* step, int n) { *step += n; }
 
@@ -119,6 +183,9 @@ struct SimHandle {
   int4* items = nullptr;
   int* order = nullptr;
   int n_items = 0;
+  // device scheduling (schedule_kernel): class of each snake, class offsets, scratch
+  int *sched_cls = nullptr, *sched_base = nullptr, *sched_hist = nullptr;
+  int n_cls = 0;
   int npl_first[5] = {0, 0, 0, 0, 0};  // items of nodes-per-lane p are [first[p-1], first[p])
   int npl_grid[4] = {0, 0, 0, 0};
   int* work = nullptr;  // [4] work-queue counters, one per solver kernel
@@ -182,12 +249,15 @@ SimStatus build_items(SimHandle* h, const std::map<int, int>* only_bucket = null
   std::vector<int> order;
   struct It { int off, cnt, lay; float cost; };
   std::vector<It> its;
+  std::vector<int> cls(h->n, -1), cls_base;
   for (auto& kv : buckets) {
     if (!h->layout.count(kv.first)) h->layout[kv.first] = default_layout(kv.first);
     if (only_bucket && !only_bucket->count(kv.first)) continue;
     const int lay = h->layout[kv.first];
     if (lay < 0) return fail(SIM_EINVAL, "snake too long for the lane layouts (max 128 nodes)");
     const int G = layout_lanes(lay), per = 32 / G;
+    for (int s : kv.second) cls[s] = (int)cls_base.size();
+    cls_base.push_back((int)order.size());
     for (size_t b = 0; b < kv.second.size(); b += per) {
       It it;
       it.off = (int)order.size();
@@ -206,14 +276,21 @@ SimStatus build_items(SimHandle* h, const std::map<int, int>* only_bucket = null
   std::vector<int4> hitems(its.size());
   for (size_t i = 0; i < its.size(); ++i) hitems[i] = make_int4(its[i].off, its[i].cnt, its[i].lay, 0);
   if (h->items) cudaFree(h->items);
-  if (h->order) cudaFree(h->order);
-  h->items = nullptr; h->order = nullptr;
+  for (int* p : {h->order, h->sched_cls, h->sched_base, h->sched_hist}) if (p) cudaFree(p);
+  h->items = nullptr;
+  h->order = h->sched_cls = h->sched_base = h->sched_hist = nullptr;
   h->n_items = (int)hitems.size();
+  h->n_cls = (int)cls_base.size();
   if (h->n_items > 0) {
     CU(cudaMalloc(&h->items, hitems.size() * sizeof(int4)));
     CU(cudaMalloc(&h->order, order.size() * sizeof(int)));
+    CU(cudaMalloc(&h->sched_cls, h->n * sizeof(int)));
+    CU(cudaMalloc(&h->sched_base, cls_base.size() * sizeof(int)));
+    CU(cudaMalloc(&h->sched_hist, cls_base.size() * 256 * sizeof(int)));
     CU(cudaMemcpy(h->items, hitems.data(), hitems.size() * sizeof(int4), cudaMemcpyHostToDevice));
     CU(cudaMemcpy(h->order, order.data(), order.size() * sizeof(int), cudaMemcpyHostToDevice));
+    CU(cudaMemcpy(h->sched_cls, cls.data(), h->n * sizeof(int), cudaMemcpyHostToDevice));
+    CU(cudaMemcpy(h->sched_base, cls_base.data(), cls_base.size() * sizeof(int), cudaMemcpyHostToDevice));
   }
   for (int p = 0; p <= 4; ++p) h->npl_first[p] = 0;
   for (size_t i = 0; i < its.size(); ++i) h->npl_first[layout_npl(its[i].lay)] = (int)i + 1;
@@ -269,6 +346,18 @@ SimStatus launch_split(SimHandle* h, int sub, cudaStream_t st) {
   return launch_args(h, A, st);
 }
 
+// Regroups the snakes of every class by the last env-step's update counts.
+SimStatus schedule(SimHandle* h, cudaStream_t st) {
+  if (h->n_items == 0) return SIM_OK;
+  SchedArgs a;
+  a.iters = h->iters; a.node_off = h->node_off_d; a.cls = h->sched_cls; a.cls_base = h->sched_base;
+  a.hist = h->sched_hist; a.order = h->order; a.n = h->n; a.n_cls = h->n_cls;
+  schedule_kernel<<<1, 1024, 0, st>>>(a);
+  CU(cudaGetLastError());
+  h->launches += 1;
+  return SIM_OK;
+}
+
 SimStatus advance(SimHandle* h, int n, cudaStream_t st) {
   advance_step_kernel<<<1, 1, 0, st>>>(h->step_dev, n);
   CU(cudaGetLastError());
@@ -278,7 +367,8 @@ SimStatus advance(SimHandle* h, int n, cudaStream_t st) {
 
 // One env-step substep by substep, with the network between solver launches.
 SimStatus split_step(SimHandle* h, cudaStream_t st) {
-  SimStatus r = launch_split(h, -1, st);
+  SimStatus r = schedule(h, st);
+  if (r == SIM_OK) r = launch_split(h, -1, st);
   for (int s = 0; s < h->cfg.n_sub && r == SIM_OK; ++s) {
     if (h->cfg.warm == SIM_WARM_LEARNED) {
       r = mlp_forward_launch(h->mlp, h->feat, h->n_nodes * 6, h->lam0, st);
@@ -300,7 +390,8 @@ SimStatus launch_steps(SimHandle* h, int n_steps, cudaStream_t st) {
     }
     return SIM_OK;
   }
-  SimStatus r = launch_args(h, make_args(h, n_steps), st);
+  SimStatus r = schedule(h, st);
+  if (r == SIM_OK) r = launch_args(h, make_args(h, n_steps), st);
   if (r == SIM_OK) r = advance(h, n_steps, st);
   return r;
 }
@@ -707,7 +798,8 @@ SimStatus sim_set_mlp(SimHandle* h, MlpHandle* m) {
 SimStatus sim_split_begin(SimHandle* h) {
   if (!h) return fail(SIM_EINVAL, "null handle");
   if (h->cur_sub >= 0) return fail(SIM_EINVAL, "an env-step is already in progress");
-  SimStatus st = launch_split(h, -1, h->stream);
+  SimStatus st = schedule(h, h->stream);
+  if (st == SIM_OK) st = launch_split(h, -1, h->stream);
   if (st != SIM_OK) return st;
   h->cur_sub = 0;
   return SIM_OK;
@@ -825,7 +917,8 @@ SimStatus sim_destroy(SimHandle* h) {
   void* ptrs[] = {h->pos, h->vel, h->press, h->lam, h->prm, h->node_off_d, h->link_off_d, h->resid,
                   h->iters, h->status, h->items, h->order, h->ucmd, h->inv_mass_d, h->scratch3,
                   h->lam0, h->feat, h->snap_pos, h->snap_vel, h->snap_press, h->snap_lam,
-                  h->step_dev, h->snap_step_dev, h->work};
+                  h->step_dev, h->snap_step_dev, h->work, h->sched_cls, h->sched_base,
+                  h->sched_hist};
   for (void* p : ptrs) if (p) cudaFree(p);
   delete h;
   return SIM_OK;
