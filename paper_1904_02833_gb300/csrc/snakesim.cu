@@ -47,14 +47,18 @@ namespace {
 }  // namespace
 
 // ------------------------------------------------------------------ kernels
-// One kernel per nodes-per-lane count (each gets the register budget of its own layout);
-// the host launches the ones that have work on forked streams so that they run together.
+// One kernel per lane layout (lanes per snake G x nodes per lane NPL): a launch then
+// runs a single code path, and the warps of an SM share their instruction cache.  (One
+// kernel for all layouts measured 5-7 issue-stall cycles per instruction waiting for
+// instructions, against under one with a kernel per layout.)  The host launches the
+// layouts that have work on forked streams, so that the next layout fills the tail of the
+// previous one.
 #ifndef SNAKE_MIN_BLOCKS
 #define SNAKE_MIN_BLOCKS 3
 #endif
-// Persistent: every warp takes the next work item (32/G snakes of one length) from a
-// counter in global memory until none is left; items are ordered longest first.
-template <int NPL, bool SPLIT>
+// Persistent: every warp takes the next work item (32/G snakes of one node count) from
+// the layout's counter in global memory until none is left.
+template <int NPL, int G, bool SPLIT>
 __global__ void __launch_bounds__(128, SNAKE_MIN_BLOCKS) snake_solver_kernel(SolverArgs A) {
   const int lane = threadIdx.x & 31;
   for (;;) {
@@ -63,47 +67,56 @@ __global__ void __launch_bounds__(128, SNAKE_MIN_BLOCKS) snake_solver_kernel(Sol
     it = __shfl_sync(0xffffffffu, it, 0);
     if (it >= A.n_items) break;
     const int4 item = A.items[it];
-    const int G = layout_lanes(item.z);
     const int gi = lane / G;
     const bool ok = gi < item.y;
     const int snake = ok ? A.order[item.x + gi] : 0;
-    if (G == 8) run_group<NPL, 8, SPLIT>(A, snake, ok);
-    else if (G == 16) run_group<NPL, 16, SPLIT>(A, snake, ok);
-    else run_group<NPL, 32, SPLIT>(A, snake, ok);
+    run_group<NPL, G, SPLIT>(A, snake, ok);
   }
 }
 
 typedef void (*SolverKernel)(SolverArgs);
-// [split][nodes per lane - 1]
-const SolverKernel kSolverKernels[2][4] = {
-    {snake_solver_kernel<1, false>, snake_solver_kernel<2, false>, snake_solver_kernel<3, false>,
-     snake_solver_kernel<4, false>},
-    {snake_solver_kernel<1, true>, snake_solver_kernel<2, true>, snake_solver_kernel<3, true>,
-     snake_solver_kernel<4, true>}};
+constexpr int kLayouts = 12;
+// [split][layout_id(G, NPL)]
+#define SNAKE_KERNELS(S)                                                                  \
+  {snake_solver_kernel<1, 8, S>,  snake_solver_kernel<2, 8, S>,  snake_solver_kernel<3, 8, S>,  \
+   snake_solver_kernel<4, 8, S>,  snake_solver_kernel<1, 16, S>, snake_solver_kernel<2, 16, S>, \
+   snake_solver_kernel<3, 16, S>, snake_solver_kernel<4, 16, S>, snake_solver_kernel<1, 32, S>, \
+   snake_solver_kernel<2, 32, S>, snake_solver_kernel<3, 32, S>, snake_solver_kernel<4, 32, S>}
+const SolverKernel kSolverKernels[2][kLayouts] = {SNAKE_KERNELS(false), SNAKE_KERNELS(true)};
+#undef SNAKE_KERNELS
 
 // ------------------------------------------------------------------ scheduling
-// Before every env-step the snakes of each node-count class are ranked on the device by
-// the Jacobi updates they needed in the previous env-step (temporal coherence), and
-// consecutive snakes of the ranking share a warp: the lane groups of a warp run in lock
-// step until the slowest one has converged, so grouping snakes of similar cost wastes
-// fewer passes, and each class's items are then queued most expensive first.  (Queueing
-// all items in one most-expensive-first order measured slower than keeping the classes
-// in their static order.)  The physics of a snake does not depend on the warp it gets.
+// Before every env-step the work queue is rebuilt on the device from the Jacobi updates
+// each snake needed in the previous env-step (temporal coherence):
+//  * inside a node-count class the snakes are ranked by that count and consecutive
+//    snakes of the ranking share a warp (the lane groups of a warp run in lock step until
+//    the slowest has converged, so similar snakes waste fewer passes);
+//  * inside every layout's queue the items are ordered most expensive first (longest-
+//    processing-time order, an item costing about its largest update count), so that
+//    the launch does not end on a few long items.
+// The physics of a snake does not depend on the warp or the queue position it gets.
 struct SchedArgs {
   const int* iters;     // [S] updates of the previous env-step (0: none yet)
   const int* node_off;  // [S + 1]
   const int* cls;       // [S] class of each snake (-1: not scheduled)
   const int* cls_base;  // [C] first slot of the class in `order`
-  int* hist;            // [C * 256] scratch
+  const int4* items0;   // [n_items] the classes' items (offset, count, layout), class by class
+  int* hist;            // [(C + 12) * 256] scratch
+  int* key;             // [n_items] scratch
   int* order;           // out: the snakes of class c at [cls_base[c], cls_base[c] + count)
-  int n, n_cls;
+  int4* items;          // out: the queue of layout l at [lay_first[l], lay_first[l + 1])
+  int n, n_cls, n_items;
+  int lay_first[12];
 };
 
-// Cost bin of a snake, 16 bins per octave of its update count (its node count before the
-// first step); bins count down so that the expensive snakes come first.
-__device__ __forceinline__ int sched_bin(const SchedArgs& a, int s) {
-  int v = a.iters[s];
-  if (v <= 0) v = a.node_off[s + 1] - a.node_off[s];
+// Predicted cost of a snake: its last update count (its node count before the first step).
+__device__ __forceinline__ int sched_cost(const SchedArgs& a, int s) {
+  const int v = a.iters[s];
+  return min(v > 0 ? v : a.node_off[s + 1] - a.node_off[s], 1 << 26);
+}
+
+// 16 bins per octave, counting down so that the expensive come first.
+__device__ __forceinline__ int sched_bin(int v) {
   v = max(v, 1);
   const int e = 31 - __clz(v);
   const int m = e >= 4 ? (v >> (e - 4)) & 15 : (v << (4 - e)) & 15;
@@ -127,21 +140,37 @@ __device__ __forceinline__ void warp_scan256(int* c) {
   for (int k = 0; k < 8; ++k) { c[lane * 8 + k] = run; run += v[k]; }
 }
 
-// One block: counting sort of the snakes by (class, cost bin).
+// One block: counting sort of the snakes by (class, cost bin), then of the items by
+// (layout, cost bin of their first = most expensive snake).
 __global__ void __launch_bounds__(1024) schedule_kernel(SchedArgs a) {
   const int t = threadIdx.x, T = blockDim.x, warp = t >> 5, nw = T >> 5;
-  for (int i = t; i < a.n_cls * 256; i += T) a.hist[i] = 0;
+  int* hi = a.hist + a.n_cls * 256;
+  for (int i = t; i < (a.n_cls + 12) * 256; i += T) a.hist[i] = 0;
   __syncthreads();
   for (int s = t; s < a.n; s += T) {
     const int c = a.cls[s];
-    if (c >= 0) atomicAdd(&a.hist[c * 256 + sched_bin(a, s)], 1);
+    if (c >= 0) atomicAdd(&a.hist[c * 256 + sched_bin(sched_cost(a, s))], 1);
   }
   __syncthreads();
   for (int r = warp; r < a.n_cls; r += nw) warp_scan256(a.hist + r * 256);
   __syncthreads();
   for (int s = t; s < a.n; s += T) {
     const int c = a.cls[s];
-    if (c >= 0) a.order[a.cls_base[c] + atomicAdd(&a.hist[c * 256 + sched_bin(a, s)], 1)] = s;
+    if (c >= 0) a.order[a.cls_base[c] + atomicAdd(&a.hist[c * 256 + sched_bin(sched_cost(a, s))], 1)] = s;
+  }
+  __syncthreads();
+  for (int k = t; k < a.n_items; k += T) {
+    const int4 it = a.items0[k];
+    const int b = sched_bin(sched_cost(a, a.order[it.x]));
+    a.key[k] = b;
+    atomicAdd(&hi[it.z * 256 + b], 1);
+  }
+  __syncthreads();
+  for (int r = warp; r < 12; r += nw) warp_scan256(hi + r * 256);
+  __syncthreads();
+  for (int k = t; k < a.n_items; k += T) {
+    const int4 it = a.items0[k];
+    a.items[a.lay_first[it.z] + atomicAdd(&hi[it.z * 256 + a.key[k]], 1)] = it;
   }
 }
 
@@ -184,13 +213,17 @@ struct SimHandle {
   int* order = nullptr;
   int n_items = 0;
   // device scheduling (schedule_kernel): class of each snake, class offsets, scratch
-  int *sched_cls = nullptr, *sched_base = nullptr, *sched_hist = nullptr;
+  int4* items0 = nullptr;
+  int *sched_cls = nullptr, *sched_base = nullptr, *sched_hist = nullptr, *sched_key = nullptr;
   int n_cls = 0;
-  int npl_first[5] = {0, 0, 0, 0, 0};  // items of nodes-per-lane p are [first[p-1], first[p])
-  int npl_grid[4] = {0, 0, 0, 0};
-  int* work = nullptr;  // [4] work-queue counters, one per solver kernel
-  cudaStream_t side[4] = {nullptr, nullptr, nullptr, nullptr};
-  cudaEvent_t ev_side[4] = {nullptr, nullptr, nullptr, nullptr};
+  int lay_first[kLayouts + 1] = {};  // items of layout l are [lay_first[l], lay_first[l + 1])
+  int lay_grid[kLayouts] = {};
+  int lay_launch[kLayouts] = {};      // layouts with work, most work first
+  int n_lay = 0;
+  int* work = nullptr;                // [kLayouts] work-queue counters
+  cudaStream_t side[kLayouts] = {};
+  cudaEvent_t ev_side[kLayouts] = {};
+  cudaEvent_t ev_split = nullptr;
   float* ucmd = nullptr;
   bool use_ucmd = false;
   float* inv_mass_d = nullptr;
@@ -268,43 +301,57 @@ SimStatus build_items(SimHandle* h, const std::map<int, int>* only_bucket = null
       its.push_back(it);
     }
   }
-  // items ordered by nodes per lane (one kernel each), longest snakes first inside
+  // items0: class by class (the scheduler's input); the first queue: by layout, longest
+  // snakes first inside (before any update counts are known)
+  std::vector<int4> items0(its.size());
+  for (size_t i = 0; i < its.size(); ++i) items0[i] = make_int4(its[i].off, its[i].cnt, its[i].lay, 0);
   std::stable_sort(its.begin(), its.end(), [](const It& a, const It& b) {
-    if (layout_npl(a.lay) != layout_npl(b.lay)) return layout_npl(a.lay) < layout_npl(b.lay);
+    if (a.lay != b.lay) return a.lay < b.lay;
     return a.cost > b.cost;
   });
   std::vector<int4> hitems(its.size());
   for (size_t i = 0; i < its.size(); ++i) hitems[i] = make_int4(its[i].off, its[i].cnt, its[i].lay, 0);
-  if (h->items) cudaFree(h->items);
-  for (int* p : {h->order, h->sched_cls, h->sched_base, h->sched_hist}) if (p) cudaFree(p);
-  h->items = nullptr;
-  h->order = h->sched_cls = h->sched_base = h->sched_hist = nullptr;
+  for (int4* p : {h->items, h->items0}) if (p) cudaFree(p);
+  for (int* p : {h->order, h->sched_cls, h->sched_base, h->sched_hist, h->sched_key}) if (p) cudaFree(p);
+  h->items = h->items0 = nullptr;
+  h->order = h->sched_cls = h->sched_base = h->sched_hist = h->sched_key = nullptr;
   h->n_items = (int)hitems.size();
   h->n_cls = (int)cls_base.size();
   if (h->n_items > 0) {
     CU(cudaMalloc(&h->items, hitems.size() * sizeof(int4)));
+    CU(cudaMalloc(&h->items0, items0.size() * sizeof(int4)));
     CU(cudaMalloc(&h->order, order.size() * sizeof(int)));
     CU(cudaMalloc(&h->sched_cls, h->n * sizeof(int)));
     CU(cudaMalloc(&h->sched_base, cls_base.size() * sizeof(int)));
-    CU(cudaMalloc(&h->sched_hist, cls_base.size() * 256 * sizeof(int)));
+    CU(cudaMalloc(&h->sched_hist, (cls_base.size() + kLayouts) * 256 * sizeof(int)));
+    CU(cudaMalloc(&h->sched_key, hitems.size() * sizeof(int)));
     CU(cudaMemcpy(h->items, hitems.data(), hitems.size() * sizeof(int4), cudaMemcpyHostToDevice));
+    CU(cudaMemcpy(h->items0, items0.data(), items0.size() * sizeof(int4), cudaMemcpyHostToDevice));
     CU(cudaMemcpy(h->order, order.data(), order.size() * sizeof(int), cudaMemcpyHostToDevice));
     CU(cudaMemcpy(h->sched_cls, cls.data(), h->n * sizeof(int), cudaMemcpyHostToDevice));
     CU(cudaMemcpy(h->sched_base, cls_base.data(), cls_base.size() * sizeof(int), cudaMemcpyHostToDevice));
   }
-  for (int p = 0; p <= 4; ++p) h->npl_first[p] = 0;
-  for (size_t i = 0; i < its.size(); ++i) h->npl_first[layout_npl(its[i].lay)] = (int)i + 1;
-  for (int p = 1; p <= 4; ++p) h->npl_first[p] = std::max(h->npl_first[p], h->npl_first[p - 1]);
+  // per-layout ranges, grids, and launch order (most nodes x nodes per lane first)
+  std::vector<double> work(kLayouts, 0.0);
+  int cnt[kLayouts] = {};
+  for (const It& it : its) { cnt[it.lay] += 1; work[it.lay] += it.cost * layout_npl(it.lay); }
+  h->lay_first[0] = 0;
+  for (int l = 0; l < kLayouts; ++l) h->lay_first[l + 1] = h->lay_first[l] + cnt[l];
   int dev = 0, sms = 0;
   CU(cudaGetDevice(&dev));
   CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  for (int p = 0; p < 4; ++p) {
+  h->n_lay = 0;
+  for (int l = 0; l < kLayouts; ++l) {
+    h->lay_grid[l] = 0;
+    if (cnt[l] == 0) continue;
     int per_sm = 0;
-    CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kSolverKernels[0][p], 128, 0));
-    const int n = h->npl_first[p + 1] - h->npl_first[p];
-    const int need = (n + 3) / 4;
-    h->npl_grid[p] = n == 0 ? 0 : std::max(1, std::min(need, std::max(1, per_sm) * sms));
+    CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kSolverKernels[0][l], 128, 0));
+    const int need = (cnt[l] + 3) / 4;  // four warps per block
+    h->lay_grid[l] = std::max(1, std::min(need, std::max(1, per_sm) * sms));
+    h->lay_launch[h->n_lay++] = l;
   }
+  std::stable_sort(h->lay_launch, h->lay_launch + h->n_lay,
+                   [&](int a, int b) { return work[a] > work[b]; });
   h->graph_dirty = true;
   return SIM_OK;
 }
@@ -315,6 +362,7 @@ SolverArgs make_args(SimHandle* h, int n_steps) {
   A.node_off = h->node_off_d; A.link_off = h->link_off_d;
   A.resid = h->resid; A.iters = h->iters; A.status = h->status;
   A.items = h->items; A.order = h->order; A.n_items = h->n_items;
+  A.work = h->work;
   A.ucmd = h->use_ucmd ? h->ucmd : nullptr;
   A.lam0 = (h->cfg.warm == SIM_WARM_LEARNED) ? h->lam0 : nullptr;
   A.feat = h->feat;
@@ -346,12 +394,14 @@ SimStatus launch_split(SimHandle* h, int sub, cudaStream_t st) {
   return launch_args(h, A, st);
 }
 
-// Regroups the snakes of every class by the last env-step's update counts.
+// Rebuilds the work queue from the last env-step's update counts.
 SimStatus schedule(SimHandle* h, cudaStream_t st) {
   if (h->n_items == 0) return SIM_OK;
   SchedArgs a;
   a.iters = h->iters; a.node_off = h->node_off_d; a.cls = h->sched_cls; a.cls_base = h->sched_base;
-  a.hist = h->sched_hist; a.order = h->order; a.n = h->n; a.n_cls = h->n_cls;
+  a.items0 = h->items0; a.hist = h->sched_hist; a.key = h->sched_key; a.order = h->order;
+  a.items = h->items; a.n = h->n; a.n_cls = h->n_cls; a.n_items = h->n_items;
+  for (int l = 0; l < kLayouts; ++l) a.lay_first[l] = h->lay_first[l];
   schedule_kernel<<<1, 1024, 0, st>>>(a);
   CU(cudaGetLastError());
   h->launches += 1;
@@ -398,25 +448,23 @@ SimStatus launch_steps(SimHandle* h, int n_steps, cudaStream_t st) {
 
 SimStatus launch_args(SimHandle* h, const SolverArgs& A, cudaStream_t st) {
   if (h->n_items == 0) return SIM_OK;
-  int kinds = 0;
-  for (int p = 0; p < 4; ++p) kinds += h->npl_grid[p] > 0;
-  bool fork = kinds > 1;
-  if (fork) CU(cudaEventRecord(h->ev_fork, st));
-  for (int p = 0; p < 4; ++p) {
-    if (h->npl_grid[p] == 0) continue;
+  const bool fork = h->n_lay > 1;
+  if (fork) CU(cudaEventRecord(h->ev_split, st));
+  for (int k = 0; k < h->n_lay; ++k) {
+    const int l = h->lay_launch[k];
     SolverArgs B = A;
-    B.items = h->items + h->npl_first[p];
-    B.n_items = h->npl_first[p + 1] - h->npl_first[p];
-    B.work = h->work + p;
-    cudaStream_t s = fork ? h->side[p] : st;
-    if (fork) CU(cudaStreamWaitEvent(s, h->ev_fork, 0));
+    B.items = h->items + h->lay_first[l];
+    B.n_items = h->lay_first[l + 1] - h->lay_first[l];
+    B.work = h->work + l;
+    cudaStream_t s = fork ? h->side[l] : st;
+    if (fork) CU(cudaStreamWaitEvent(s, h->ev_split, 0));
     CU(cudaMemsetAsync(B.work, 0, sizeof(int), s));
-    kSolverKernels[A.split ? 1 : 0][p]<<<h->npl_grid[p], 128, 0, s>>>(B);
+    kSolverKernels[A.split ? 1 : 0][l]<<<h->lay_grid[l], 128, 0, s>>>(B);
     CU(cudaGetLastError());
     h->launches += 1;
     if (fork) {
-      CU(cudaEventRecord(h->ev_side[p], s));
-      CU(cudaStreamWaitEvent(st, h->ev_side[p], 0));
+      CU(cudaEventRecord(h->ev_side[l], s));
+      CU(cudaStreamWaitEvent(st, h->ev_side[l], 0));
     }
   }
   return SIM_OK;
@@ -496,7 +544,7 @@ SimStatus sim_create(const SimConfig* cfg, int n_snakes, const SnakeParams* para
   ALLOC(h->scratch3, h->n_nodes * 6 * sizeof(float));
   ALLOC(h->lam0, h->n_nodes * 6 * sizeof(float));
   ALLOC(h->step_dev, sizeof(long long));
-  ALLOC(h->work, 4 * sizeof(int));
+  ALLOC(h->work, kLayouts * sizeof(int));
   ALLOC(h->feat, h->n_nodes * 6 * 32 * sizeof(__nv_bfloat16));
 #undef ALLOC
 #define CUC(call)                                                                         \
@@ -517,9 +565,10 @@ SimStatus sim_create(const SimConfig* cfg, int n_snakes, const SnakeParams* para
   CUC(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
   CUC(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
   CUC(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
-  for (int p = 0; p < 4; ++p) {
-    CUC(cudaStreamCreateWithFlags(&h->side[p], cudaStreamNonBlocking));
-    CUC(cudaEventCreateWithFlags(&h->ev_side[p], cudaEventDisableTiming));
+  CUC(cudaEventCreateWithFlags(&h->ev_split, cudaEventDisableTiming));
+  for (int l = 0; l < kLayouts; ++l) {
+    CUC(cudaStreamCreateWithFlags(&h->side[l], cudaStreamNonBlocking));
+    CUC(cudaEventCreateWithFlags(&h->ev_side[l], cudaEventDisableTiming));
   }
 #undef CUC
   st = build_items(h);
@@ -910,15 +959,16 @@ SimStatus sim_destroy(SimHandle* h) {
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
   if (h->ev_join) cudaEventDestroy(h->ev_join);
-  for (int p = 0; p < 4; ++p) {
-    if (h->side[p]) cudaStreamDestroy(h->side[p]);
-    if (h->ev_side[p]) cudaEventDestroy(h->ev_side[p]);
+  if (h->ev_split) cudaEventDestroy(h->ev_split);
+  for (int l = 0; l < kLayouts; ++l) {
+    if (h->side[l]) cudaStreamDestroy(h->side[l]);
+    if (h->ev_side[l]) cudaEventDestroy(h->ev_side[l]);
   }
   void* ptrs[] = {h->pos, h->vel, h->press, h->lam, h->prm, h->node_off_d, h->link_off_d, h->resid,
                   h->iters, h->status, h->items, h->order, h->ucmd, h->inv_mass_d, h->scratch3,
                   h->lam0, h->feat, h->snap_pos, h->snap_vel, h->snap_press, h->snap_lam,
                   h->step_dev, h->snap_step_dev, h->work, h->sched_cls, h->sched_base,
-                  h->sched_hist};
+                  h->sched_hist, h->sched_key, h->items0};
   for (void* p : ptrs) if (p) cudaFree(p);
   delete h;
   return SIM_OK;
