@@ -73,7 +73,22 @@ typedef struct {
   float beta;         /* weight of the previous substep's multipliers in a warm start:   *
                        * PREVIOUS starts from beta lambda_prev, LEARNED from              *
                        * beta lambda_prev + m g h^2 y (y: the network's output)          */
+  int32_t latency;    /* chamber model, SIM_LATENCY_*                                    */
+  /* SIM_LATENCY_LAW only (Sec. V-A, Eq. 11-12; pressures in units of the maximum):      *
+   * every law_dt seconds (rounded to whole substeps, at least one) each chamber moves    *
+   * towards its target p^ at the end of that period: inflating by                        *
+   * p_source k_inflate ((p^ - p) / p_source)^2, deflating by min(p k_deflate, t_p),      *
+   * never past p^; it holds its value in between.                                        */
+  float k_inflate;    /* (0, 1]; the paper's fitted value 0.23                           */
+  float k_deflate;    /* (0, 1]; the paper's fitted value 0.23                           */
+  float t_p;          /* > 0; the paper's 0.68 psi of an 8 psi maximum = 0.085           */
+  float p_source;     /* > 0; source pressure                                            */
+  float law_dt;       /* >= 0 [s]; the paper's time step 0.0083 s                        */
 } SimConfig;
+
+/* Chamber models: first-order latency with the per-snake tau_inf / tau_def (exact
+ * exponential relaxation every substep), or the paper's discrete law (Sec. V-A). */
+enum { SIM_LATENCY_EXP = 0, SIM_LATENCY_LAW = 1 };
 
 /* Per-snake parameters (host layout, 96 bytes). */
 typedef struct {

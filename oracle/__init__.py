@@ -71,7 +71,10 @@ def pack_params(w: dict) -> np.ndarray:
 def pack_cfg(s: dict) -> np.ndarray:
     g = s["gravity"]
     return np.array([s["dt"], s["n_sub"], s["iters"], s["tol"], s["omega"], g[0], g[1], g[2],
-                     1.0 if s["contact"] else 0.0, s["warm"], s.get("beta", 1.0)], np.float64)
+                     1.0 if s["contact"] else 0.0, s["warm"], s.get("beta", 1.0),
+                     s.get("latency", 0), s.get("k_inflate", 0.23), s.get("k_deflate", 0.23),
+                     s.get("t_p", 0.085), s.get("p_source", 1.0), s.get("law_dt", 0.0083)],
+                    np.float64)
 
 
 class OracleSim:
@@ -86,6 +89,7 @@ class OracleSim:
         self.nfix = np.ascontiguousarray(w["n_fixed"], np.int32)
         self.prm = pack_params(w)
         self.cfg = pack_cfg(self.s)
+        assert len(self.cfg) == lib().oracle_ncfg()
         nn = self.nl.astype(np.int64) * self.seg + 1
         self.node_off = np.concatenate([[0], np.cumsum(nn)])
         self.link_off = np.concatenate([[0], np.cumsum(self.nl)])

@@ -100,7 +100,8 @@ template <class T> inline T dot(const V3<T>& a, const V3<T>& b) { return a.x * b
 enum { P_L0, P_MASS, P_ALPHA_S, P_ALPHA_B, P_GAIN, P_TAU_INF, P_TAU_DEF, P_MU, P_DAMP,
        P_RADIUS, P_AMP, P_FREQ, P_LAG, P_OFFSET, P_SCALE, P_ALT, P_X0, P_Y0, P_Z0, P_YAW0,
        NPRM };
-enum { C_DT, C_NSUB, C_ITERS, C_TOL, C_OMEGA, C_GX, C_GY, C_GZ, C_CONTACT, C_WARM, C_BETA, NCFG };
+enum { C_DT, C_NSUB, C_ITERS, C_TOL, C_OMEGA, C_GX, C_GY, C_GZ, C_CONTACT, C_WARM, C_BETA,
+       C_LATENCY, C_KI, C_KD, C_TP, C_PS, C_LAW_DT, NCFG };
 // Row kinds; a node i owns one multiplier slot per kind: stretch (i, i+1), yaw and
 // pitch bend centred on i, contact of i, friction of i along world x and y.
 enum { R_STRETCH, R_YAW, R_PITCH, R_CONTACT, R_FX, R_FY, NK };
@@ -129,13 +130,37 @@ Snake<T> load_snake(const int* nl, const int* seg, const int* nfix, const double
 struct Cfg {
   double dt, h, tol, omega, g[3], beta;
   int n_sub, iters, contact, warm;
+  int latency, law_every;        // chamber model (0 exponential, 1 Sec. V-A law), its period
+  double k_i, k_d, t_p, p_s;     // Sec. V-A law: gains, deflation threshold, source pressure
 };
 Cfg load_cfg(const double* c) {
   Cfg C;
   C.dt = c[C_DT]; C.n_sub = (int)c[C_NSUB]; C.h = C.dt / C.n_sub; C.iters = (int)c[C_ITERS];
   C.tol = c[C_TOL]; C.omega = c[C_OMEGA]; C.g[0] = c[C_GX]; C.g[1] = c[C_GY]; C.g[2] = c[C_GZ];
   C.contact = (int)c[C_CONTACT]; C.warm = (int)c[C_WARM]; C.beta = c[C_BETA];
+  C.latency = (int)c[C_LATENCY]; C.k_i = c[C_KI]; C.k_d = c[C_KD]; C.t_p = c[C_TP]; C.p_s = c[C_PS];
+  // the law's time step in whole substeps (at least one)
+  C.law_every = std::max(1, (int)std::llround(c[C_LAW_DT] / C.h));
   return C;
+}
+
+// One step of the chamber law of Sec. V-A (Eq. 11-12) towards the target p^: inflating
+// (p^ > p) adds p_s dp^2 k_i with dp = (p^ - p) / p_s, deflating (p^ < p) removes
+// min(p k_d, T_p); the valve stops at the target (clamp).
+template <class T>
+T chamber_law(const T& p, double tgt, const Cfg& C) {
+  const double pv = val(p);
+  if (tgt > pv) {
+    T dp = (T(tgt) - p) / C.p_s;
+    T q = p + C.p_s * dp * dp * C.k_i;
+    return val(q) > tgt ? T(tgt) : q;
+  }
+  if (tgt < pv) {
+    T dec = (pv * C.k_d < C.t_p) ? p * C.k_d : T(C.t_p);
+    T q = p - dec;
+    return val(q) < tgt ? T(tgt) : q;
+  }
+  return p;
 }
 
 // ---------------------------------------------------------------- gait (Eq. 9)
@@ -476,11 +501,18 @@ double snake_step(const Snake<T>& S, const Cfg& C, long long step_index, V3<T>* 
     // (a2) antagonistic chambers (Sec. III): a > 0 inflates the right chamber, a < 0 the
     // left; each chamber follows its target through a first-order latency,
     // p <- p^ + (p - p^) exp(-h / tau), tau = tau_inflate when rising else tau_deflate.
-    for (int k = 0; k < S.L; ++k) {
-      double a = ucmd ? ucmd[k] : gait_target(S, k, tnext);
+    // With the chamber law of Sec. V-A instead (C.latency == 1) the chambers move once
+    // per law step of C.law_every substeps, towards the target at the end of that step,
+    // and hold their value in between.
+    const long long g = step_index * C.n_sub + s;
+    const bool law_now = C.latency == 1 && g % C.law_every == 0;
+    const double tlaw = (double)(g + C.law_every) * h;
+    for (int k = 0; k < S.L && (C.latency == 0 || law_now); ++k) {
+      double a = ucmd ? ucmd[k] : gait_target(S, k, C.latency == 0 ? tnext : tlaw);
       double tgt[2] = {std::max(a, 0.0), std::max(-a, 0.0)};
       for (int ch = 0; ch < 2; ++ch) {
         T& p = press[2 * k + ch];
+        if (C.latency == 1) { p = chamber_law(p, tgt[ch], C); continue; }
         T tau = (tgt[ch] > val(p)) ? S.tau_inf : S.tau_def;
         p = tgt[ch] + (p - tgt[ch]) * exp(T(-h) / tau);
       }

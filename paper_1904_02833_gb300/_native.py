@@ -20,7 +20,10 @@ class SimConfig(ctypes.Structure):
     _fields_ = [("dt", ctypes.c_double), ("n_sub", ctypes.c_int32), ("iters", ctypes.c_int32),
                 ("tol", ctypes.c_float), ("omega", ctypes.c_float),
                 ("gravity", ctypes.c_float * 3), ("contact", ctypes.c_int32),
-                ("warm", ctypes.c_int32), ("beta", ctypes.c_float)]
+                ("warm", ctypes.c_int32), ("beta", ctypes.c_float),
+                ("latency", ctypes.c_int32), ("k_inflate", ctypes.c_float),
+                ("k_deflate", ctypes.c_float), ("t_p", ctypes.c_float),
+                ("p_source", ctypes.c_float), ("law_dt", ctypes.c_float)]
 
 
 SNAKE_FLOAT_FIELDS = ("L0", "mass", "alpha_s", "alpha_b", "gain", "tau_inf", "tau_def", "mu",
@@ -35,7 +38,7 @@ class SnakeParams(ctypes.Structure):
 
 
 assert ctypes.sizeof(SnakeParams) == 96
-assert ctypes.sizeof(SimConfig) == 48
+assert ctypes.sizeof(SimConfig) == 72
 
 _lib = None
 P = ctypes.c_void_p

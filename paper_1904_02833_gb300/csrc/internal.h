@@ -50,6 +50,9 @@ struct SolverArgs {
   int contact;
   int warm;
   float beta;
+  int latency;            // SIM_LATENCY_*
+  int law_every;          // SIM_LATENCY_LAW: substeps per law step
+  float k_i, k_d, t_p, p_s;
 };
 
 // Calibration (adjoint) state of a simulator, defined in adjoint.cu.

@@ -261,6 +261,13 @@ SimStatus validate_cfg(const SimConfig* c) {
       c->warm < 0 || c->warm > 2 || !(c->beta >= 0.f && c->beta <= 1.f))
     return fail(SIM_EINVAL, "invalid config (dt > 0, n_sub >= 1, iters >= 0, tol >= 0, omega > 0, "
                             "warm in 0..2, beta in [0, 1])");
+  if (c->latency != SIM_LATENCY_EXP && c->latency != SIM_LATENCY_LAW)
+    return fail(SIM_EINVAL, "invalid config: latency must be SIM_LATENCY_EXP or SIM_LATENCY_LAW");
+  if (c->latency == SIM_LATENCY_LAW &&
+      (!(c->k_inflate > 0.f && c->k_inflate <= 1.f) || !(c->k_deflate > 0.f && c->k_deflate <= 1.f) ||
+       !(c->t_p > 0.f) || !(c->p_source > 0.f) || !(c->law_dt >= 0.f)))
+    return fail(SIM_EINVAL, "invalid chamber law (k_inflate, k_deflate in (0, 1], t_p > 0, "
+                            "p_source > 0, law_dt >= 0)");
   return SIM_OK;
 }
 
@@ -381,6 +388,9 @@ SolverArgs make_args(SimHandle* h, int n_steps) {
   A.contact = h->cfg.contact;
   A.warm = h->cfg.warm;
   A.beta = h->cfg.beta;
+  A.latency = h->cfg.latency;
+  A.law_every = std::max(1, (int)std::llround((double)h->cfg.law_dt / A.h_d));
+  A.k_i = h->cfg.k_inflate; A.k_d = h->cfg.k_deflate; A.t_p = h->cfg.t_p; A.p_s = h->cfg.p_source;
   return A;
 }
 
@@ -921,6 +931,8 @@ SimStatus sim_calib_forward(SimHandle* h, const float* theta, int n_steps, int c
   if (!h || !theta || !tips) return fail(SIM_EINVAL, "null handle or buffer");
   if (n_steps < 1 || ckpt_every < 1) return fail(SIM_EINVAL, "n_steps and ckpt_every must be >= 1");
   if (h->cur_sub >= 0) return fail(SIM_EINVAL, "a split env-step is in progress (sim_split_finish)");
+  if (h->cfg.latency != SIM_LATENCY_EXP)
+    return fail(SIM_EINVAL, "calibration differentiates the first-order chamber model only");
   if (!h->calib) h->calib = calib_new();
   std::string err;
   SimStatus st = calib_forward(*h->calib, h->prm, h->node_off_d, h->link_off_d, h->n, h->max_nodes,

@@ -426,6 +426,17 @@ __device__ __forceinline__ void write_features(const SnakeK& S, const SolverArgs
   }
 }
 
+// One step of the chamber law of Sec. V-A (Eq. 11-12) towards the target t: inflating
+// adds p_s k_i ((t - p) / p_s)^2, deflating removes min(p k_d, T_p), never past t.
+__device__ __forceinline__ float chamber_law(float p, float t, const SolverArgs& A) {
+  if (t > p) {
+    const float dp = (t - p) / A.p_s;
+    return fminf(t, p + A.p_s * dp * dp * A.k_i);
+  }
+  if (t < p) return fmaxf(t, p - fminf(p * A.k_d, A.t_p));
+  return p;
+}
+
 // Advances the snake owned by this lane group.  Fused mode (A.split == 0): A.n_steps
 // env-steps with all substeps in registers.  Split mode: finishes substep A.sub (if >= 0)
 // of the current env-step and, if A.sub + 1 < n_sub, begins substep A.sub + 1 (gait,
@@ -486,7 +497,12 @@ __device__ void run_group(const SolverArgs& A, int snake, bool valid) {
   // (a1) gait target at the end of substep s, (a2) chamber latency, (a3) rest angle,
   // (a4) predict: the substep starts at x = xs + dx; dx restarts at h v
   auto begin_substep = [&](long long step, int s) {
-    const double tp = ((double)step * A.n_sub + (double)(s + 1)) * A.h_d;
+    // first-order model: target at the end of the substep, every substep; the law of
+    // Sec. V-A: once per law step, target at the end of the law step, held in between
+    const long long gsub = step * A.n_sub + s;
+    const bool law = A.latency == SIM_LATENCY_LAW;
+    const bool move = !law || gsub % A.law_every == 0;
+    const double tp = (double)(law ? gsub + A.law_every : gsub + 1) * A.h_d;
     double cyc = (double)P.gait_freq * tp;
     cyc -= floor(cyc);
     const float phase = 6.283185307179586f * (float)cyc;
@@ -495,18 +511,25 @@ __device__ void run_group(const SolverArgs& A, int snake, bool valid) {
       const int i = q * NPL + j;
       if (!(valid && i < S.N)) continue;
       const int kl = min(i / S.seg, S.L - 1);
-      float u;
-      if (A.ucmd) {
-        u = A.ucmd[S.lb + kl];
-      } else {
-        float a = P.gait_offset + P.gait_scale * sinf(phase + (float)kl * P.gait_lag);
-        a = fminf(1.f, fmaxf(-1.f, a)) * P.gait_amp;
-        if (P.gait_alternate != 0.f && (kl & 1)) a = -a;
-        u = a;
+      if (move) {
+        float u;
+        if (A.ucmd) {
+          u = A.ucmd[S.lb + kl];
+        } else {
+          float a = P.gait_offset + P.gait_scale * sinf(phase + (float)kl * P.gait_lag);
+          a = fminf(1.f, fmaxf(-1.f, a)) * P.gait_amp;
+          if (P.gait_alternate != 0.f && (kl & 1)) a = -a;
+          u = a;
+        }
+        const float tR = fmaxf(u, 0.f), tL = fmaxf(-u, 0.f);
+        if (law) {
+          pR[j] = chamber_law(pR[j], tR, A);
+          pL[j] = chamber_law(pL[j], tL, A);
+        } else {
+          pR[j] = tR + (pR[j] - tR) * (tR > pR[j] ? S.e_inf : S.e_def);
+          pL[j] = tL + (pL[j] - tL) * (tL > pL[j] ? S.e_inf : S.e_def);
+        }
       }
-      const float tR = fmaxf(u, 0.f), tL = fmaxf(-u, 0.f);
-      pR[j] = tR + (pR[j] - tR) * (tR > pR[j] ? S.e_inf : S.e_def);
-      pL[j] = tL + (pL[j] - tL) * (tL > pL[j] ? S.e_inf : S.e_def);
       th[j] = (i % S.seg == 0) ? 0.f : S.gain * (pR[j] - pL[j]) * S.L0;
     }
 #pragma unroll

@@ -50,6 +50,12 @@ def make_config(s: dict) -> N.SimConfig:
     c.contact = 1 if s["contact"] else 0
     c.warm = int(s["warm"])
     c.beta = float(s.get("beta", 1.0))
+    c.latency = int(s.get("latency", 0))
+    c.k_inflate = float(s.get("k_inflate", 0.23))
+    c.k_deflate = float(s.get("k_deflate", 0.23))
+    c.t_p = float(s.get("t_p", 0.085))
+    c.p_source = float(s.get("p_source", 1.0))
+    c.law_dt = float(s.get("law_dt", 0.0083))
     return c
 
 

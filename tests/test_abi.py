@@ -41,6 +41,7 @@ def test_struct_layout_matches_header(tmp_path):
     c.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "snakesim.h"\nint main(void){'
                  'printf("%zu\\n%zu\\n", sizeof(SimConfig), sizeof(SnakeParams));'
                  'printf("%zu\\n%zu\\n", offsetof(SimConfig, tol), offsetof(SimConfig, warm));'
+                 'printf("%zu\\n", offsetof(SimConfig, law_dt));'
                  + body + "return 0;}\n")
     exe = tmp_path / "sz"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(c), "-o", str(exe)], check=True)
@@ -48,7 +49,8 @@ def test_struct_layout_matches_header(tmp_path):
     assert out[0] == ctypes.sizeof(N.SimConfig)
     assert out[1] == ctypes.sizeof(N.SnakeParams)
     assert out[2] == N.SimConfig.tol.offset and out[3] == N.SimConfig.warm.offset
-    for f, off in zip(fields, out[4:]):
+    assert out[4] == N.SimConfig.law_dt.offset
+    for f, off in zip(fields, out[5:]):
         assert getattr(N.SnakeParams, f).offset == off, f
 
 
@@ -72,6 +74,11 @@ def test_argument_validation_without_gpu(lib):
     assert lib.sim_create(ctypes.byref(cfg), 1, long, None, ctypes.byref(h)) == N.SIM_EINVAL
     cfg2 = make_config(W.solver_settings(n_sub=0))
     assert lib.sim_create(ctypes.byref(cfg2), 1, prm, None, ctypes.byref(h)) == N.SIM_EINVAL
+    for bad_law in (dict(latency=2), dict(latency=1, k_inflate=0.0), dict(latency=1, k_deflate=1.5),
+                    dict(latency=1, t_p=0.0), dict(latency=1, p_source=-1.0), dict(latency=1, law_dt=-1.0)):
+        cfg3 = make_config(W.solver_settings(**bad_law))
+        assert lib.sim_create(ctypes.byref(cfg3), 1, prm, None, ctypes.byref(h)) == N.SIM_EINVAL, bad_law
+    assert b"law" in lib.sim_last_error() or b"latency" in lib.sim_last_error()
     assert lib.sim_create(ctypes.byref(cfg), 1, prm, None, None) == N.SIM_EINVAL
     # calls on a null handle
     assert lib.sim_step(None, 1) == N.SIM_EINVAL

@@ -197,6 +197,19 @@ def test_command_override_matches_oracle():
     compare(g, o)
 
 
+@pytest.mark.parametrize("law_dt", [0.0083, 0.0])
+def test_chamber_law_matches_oracle(law_dt):
+    """The discrete chamber law of Sec. V-A (every 10 substeps, and every substep) on a
+    ragged batch, GPU against the oracle, through a gait that inflates and deflates."""
+    w = W.batched(n=48, seed=36, links=(1, 8))
+    s = W.solver_settings(iters=10, latency=1, law_dt=law_dt)
+    g, o = Sim(w, s), oracle.OracleSim(w, s)
+    for _ in range(3):
+        g.step(2)
+        o.step(2)
+        compare(g, o)
+
+
 def test_graph_replay_is_bitwise_identical_to_direct_launch():
     w = ragged_batch()
     s = W.solver_settings(iters=10)

@@ -68,6 +68,64 @@ def test_gait_hand_values():
         assert o.press[k, 1] == pytest.approx(pL, abs=1e-12), (form, k)
 
 
+def test_chamber_law_hand_values():
+    """The discrete chamber law of Sec. V-A against sequences worked by hand
+    (tests/golden/chamber_law_hand_values.txt): inflation by the square of the remaining
+    difference, deflation linear up to the threshold T_p and proportional below it,
+    the valve stopping at the target, antagonistic chambers, the law's period."""
+    rows = [l.split() for l in open(os.path.join(HERE, "golden", "chamber_law_hand_values.txt"))
+            if l.strip() and not l.startswith("#")]
+    for case, ki, kd, tp, ps, every, u, pr0, pl0, n, pr, pl in rows:
+        w = one(W.single_snake(), n_links=1, gait_alternate=0.0)
+        dt = 1.0 / 60.0
+        s = W.solver_settings(dt=dt, n_sub=1, iters=1, gravity=(0, 0, 0), contact=False, latency=1,
+                              k_inflate=float(ki), k_deflate=float(kd), t_p=float(tp),
+                              p_source=float(ps), law_dt=int(every) * dt)
+        o = oracle.OracleSim(w, s)
+        o.press[0] = [float(pr0), float(pl0)]
+        o.step(int(n), ucmd=np.array([float(u)]))
+        assert o.press[0, 0] == pytest.approx(float(pr), abs=1e-15), (case, n)
+        assert o.press[0, 1] == pytest.approx(float(pl), abs=1e-15), (case, n)
+
+
+def test_chamber_law_closed_forms():
+    """Closed forms of the law: below the threshold (p k_d < T_p) deflation is geometric,
+    p_n = p_0 (1 - k_d)^n; above it, linear, p_n = p_0 - n T_p; inflation satisfies the
+    discrete Riccati identity 1/d' = 1/d + k_i/p_s + k_i^2 d / (p_s^2 (1 - k_i d / p_s))
+    for the remaining difference d = p^ - p; within a law period the chambers hold."""
+    w = one(W.single_snake(), n_links=1, gait_alternate=0.0)
+    dt = 1.0 / 60.0
+    base = dict(dt=dt, n_sub=1, iters=1, gravity=(0, 0, 0), contact=False, latency=1)
+    o = oracle.OracleSim(w, W.solver_settings(**base, k_deflate=0.3, t_p=0.5, law_dt=dt))
+    o.press[0] = [0.9, 0.0]
+    for n in range(1, 30):
+        o.step(1, ucmd=np.array([0.0]))
+        assert o.press[0, 0] == pytest.approx(0.9 * 0.7 ** n, rel=1e-12)
+    o = oracle.OracleSim(w, W.solver_settings(**base, k_deflate=0.9, t_p=0.05, law_dt=dt))
+    o.press[0] = [1.0, 0.0]
+    for n in range(1, 15):  # p k_d >= T_p while p >= 0.0556
+        o.step(1, ucmd=np.array([0.0]))
+        assert o.press[0, 0] == pytest.approx(1.0 - 0.05 * n, abs=1e-12)
+    ki, ps, tgt = 0.37, 1.3, 0.8
+    o = oracle.OracleSim(w, W.solver_settings(**base, k_inflate=ki, p_source=ps, law_dt=dt))
+    d = tgt
+    for n in range(40):
+        o.step(1, ucmd=np.array([tgt]))
+        d_new = tgt - o.press[0, 0]
+        expect = 1.0 / d + ki / ps + ki * ki * d / (ps * ps * (1.0 - ki * d / ps))
+        assert 1.0 / d_new == pytest.approx(expect, rel=1e-9)
+        d = d_new
+    # period of 5 substeps inside a 20-substep env-step: four moves per env-step
+    s = W.solver_settings(**dict(base, n_sub=20), k_inflate=0.5, law_dt=5 * dt / 20)
+    o = oracle.OracleSim(w, s)
+    o.step(1, ucmd=np.array([1.0]))
+    p, d = 0.0, 1.0
+    for _ in range(4):
+        p += 0.5 * d * d
+        d = 1.0 - p
+    assert o.press[0, 0] == pytest.approx(p, rel=1e-14)
+
+
 # ------------------------------------------------------------------ geometry of the rows
 def _settle(o, steps, ucmd=None):
     for _ in range(steps):
