@@ -67,6 +67,15 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
   __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
   return *reinterpret_cast<uint32_t*>(&h);
 }
+// silu of two values, evaluated in bfloat16 pairs (the result feeds a bfloat16 operand
+// anyway): silu(z) = hz + hz tanh(hz) with hz = z / 2, one packed tanh for two values.
+__device__ __forceinline__ uint32_t silu_bf16x2(float z0, float z1) {
+  const uint32_t hz = pack_bf16x2(0.5f * z0, 0.5f * z1);
+  uint32_t th, r;
+  asm("tanh.approx.bf16x2 %0, %1;" : "=r"(th) : "r"(hz));
+  asm("fma.rn.bf16x2 %0, %1, %2, %1;" : "=r"(r) : "r"(hz), "r"(th));
+  return r;
+}
 __device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
   asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};\n" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d)
                : "memory");
@@ -101,24 +110,32 @@ struct InferSmem {
   uint8_t x[kTile * kInPad * 2];
   uint8_t h[kTile * kHid * 2];
   float b1[kHid], b2[kHid], w3[kHid];
+  float part[kTile];  // second column half's share of y, per row
   uint64_t mbar;
   uint32_t tmem;
 };
+constexpr int kInferThreads = 256;
 
 }  // namespace
 
 // y[r] = w3 . silu(W2 silu(W1 x_r + b1) + b2) + b3 for feat [rows][32] bf16.
-__global__ void __launch_bounds__(128) mlp_infer_kernel(const __nv_bfloat16* __restrict__ feat,
-                                                        long long rows, MlpDev w,
-                                                        float* __restrict__ out, int* err) {
+// Eight warps per block, two blocks per SM: warp w reads TMEM lane quarter w % 4 (rows
+// 32 (w % 4) .. +31) and takes the column half w / 4 of both epilogues, so each row's
+// 256 SiLU evaluations are split between two threads; the next tile's features are
+// loaded into registers while the current tile's MMAs run.
+__global__ void __launch_bounds__(kInferThreads, 2) mlp_infer_kernel(const __nv_bfloat16* __restrict__ feat,
+                                                                    long long rows, MlpDev w,
+                                                                    float* __restrict__ out, int* err) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   InferSmem& S = *reinterpret_cast<InferSmem*>(smem_raw);
-  const int t = threadIdx.x, warp = t >> 5;
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  const int quad = warp & 3, half = warp >> 2;
+  const int row = quad * 32 + lane;  // the TMEM lane (tile row) this thread reads
   if (warp == 0) tc::tmem_alloc(&S.tmem, 256);
   if (t == 0) tc::mbar_init(&S.mbar, 1);
   stage_kmajor(S.w1, w.w1, kHid, kInPad);
   stage_kmajor(S.w2, w.w2, kHid, kHid);
-  S.b1[t] = w.b1[t]; S.b2[t] = w.b2[t]; S.w3[t] = w.w3[t];
+  if (t < kHid) { S.b1[t] = w.b1[t]; S.b2[t] = w.b2[t]; S.w3[t] = w.w3[t]; }
   const float b3 = w.b3[0];
   tc::fence_proxy_async();
   asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
@@ -126,24 +143,31 @@ __global__ void __launch_bounds__(128) mlp_infer_kernel(const __nv_bfloat16* __r
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = S.tmem;
-  const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+  const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
   const uint32_t idesc = tc::make_idesc_bf16(kTile, kHid);
   const uint32_t sx = tc::smem_u32(S.x), sh = tc::smem_u32(S.h);
   const uint32_t sw1 = tc::smem_u32(S.w1), sw2 = tc::smem_u32(S.w2);
   uint32_t phase = 0;
   bool ok = true;
   const long long ntiles = (rows + kTile - 1) / kTile;
-  for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-    // stage the feature tile (row t per thread)
-    const long long r = tile * kTile + t;
-    uint4 v[4] = {};
-    if (r < rows) {
-      const uint4* src = reinterpret_cast<const uint4*>(feat + r * kInPad);
+  // a tile is 128 rows x 4 chunks of 16 bytes: chunks t and t + 256 of this thread
+  auto load_tile = [&](long long tile, uint4 (&v)[2]) {
 #pragma unroll
-      for (int q = 0; q < 4; ++q) v[q] = src[q];
+    for (int u = 0; u < 2; ++u) {
+      const int c = t + u * kInferThreads;
+      const long long r = tile * kTile + (c >> 2);
+      v[u] = make_uint4(0u, 0u, 0u, 0u);
+      if (tile < ntiles && r < rows) v[u] = reinterpret_cast<const uint4*>(feat + r * kInPad)[c & 3];
     }
+  };
+  uint4 nxt[2];
+  load_tile(blockIdx.x, nxt);
+  for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
 #pragma unroll
-    for (int q = 0; q < 4; ++q) st_shared_v4(sx + tc::kmajor_off(t, 8 * q, kInPad), v[q].x, v[q].y, v[q].z, v[q].w);
+    for (int u = 0; u < 2; ++u) {
+      const int c = t + u * kInferThreads;
+      st_shared_v4(sx + tc::kmajor_off(c >> 2, 8 * (c & 3), kInPad), nxt[u].x, nxt[u].y, nxt[u].z, nxt[u].w);
+    }
     tc::fence_proxy_async();
     tc::fence_before_sync();
     __syncthreads();
@@ -155,12 +179,13 @@ __global__ void __launch_bounds__(128) mlp_infer_kernel(const __nv_bfloat16* __r
                      tc::make_sdesc(sw1 + kk * 256, 128, kInPad / 8 * 128), idesc, kk > 0);
       tc::mma_commit(&S.mbar);
     }
+    load_tile(tile + gridDim.x, nxt);  // in flight while the tensor core works
     if (__syncthreads_or(!tc::mbar_wait(&S.mbar, phase, kWaitLimit))) { ok = false; break; }
     phase ^= 1;
     tc::fence_after_sync();
     // epilogue 1: h = silu(z1 + b1) -> bf16 -> shared (A operand of the second GEMM)
 #pragma unroll 1
-    for (int c0 = 0; c0 < kHid; c0 += 32) {
+    for (int c0 = half * 64; c0 < half * 64 + 64; c0 += 32) {
       float a[32];
       tc::tmem_ld32(tmem + lane_base + c0, a);
 #pragma unroll
@@ -169,9 +194,9 @@ __global__ void __launch_bounds__(128) mlp_infer_kernel(const __nv_bfloat16* __r
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
           const int c = c0 + 8 * q + 2 * e;
-          p[e] = pack_bf16x2(silu(a[8 * q + 2 * e] + S.b1[c]), silu(a[8 * q + 2 * e + 1] + S.b1[c + 1]));
+          p[e] = silu_bf16x2(a[8 * q + 2 * e] + S.b1[c], a[8 * q + 2 * e + 1] + S.b1[c + 1]);
         }
-        st_shared_v4(sh + tc::kmajor_off(t, c0 + 8 * q, kHid), p[0], p[1], p[2], p[3]);
+        st_shared_v4(sh + tc::kmajor_off(row, c0 + 8 * q, kHid), p[0], p[1], p[2], p[3]);
       }
     }
     tc::fence_proxy_async();
@@ -188,19 +213,21 @@ __global__ void __launch_bounds__(128) mlp_infer_kernel(const __nv_bfloat16* __r
     if (__syncthreads_or(!tc::mbar_wait(&S.mbar, phase, kWaitLimit))) { ok = false; break; }
     phase ^= 1;
     tc::fence_after_sync();
-    // epilogue 2: y = w3 . silu(z2 + b2) + b3
-    float y = b3;
+    // epilogue 2: y = w3 . silu(z2 + b2) + b3, the two column halves added through shared
+    float y = 0.f;
 #pragma unroll 1
-    for (int c0 = 0; c0 < kHid; c0 += 32) {
+    for (int c0 = half * 64; c0 < half * 64 + 64; c0 += 32) {
       float a[32];
       tc::tmem_ld32(tmem + lane_base + kHid + c0, a);
 #pragma unroll
       for (int i = 0; i < 32; ++i) y = fmaf(S.w3[c0 + i], silu(a[i] + S.b2[c0 + i]), y);
     }
-    if (r < rows) out[r] = y;
+    if (half == 1) S.part[row] = y;
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
+    const long long r = tile * kTile + row;
+    if (half == 0 && r < rows) out[r] = (y + S.part[row]) + b3;
   }
   if (!ok) {
     if (t == 0) atomicExch(err, 1);
@@ -506,7 +533,8 @@ SimStatus snakesim::mlp_forward_launch(MlpHandle* h, const void* feat, long long
   if (rows <= 0) return SIM_OK;
   const long long tiles = (rows + kTile - 1) / kTile;
   const int grid = (int)std::min<long long>(tiles, 2LL * h->sms);
-  mlp_infer_kernel<<<grid, 128, sizeof(InferSmem), st>>>((const __nv_bfloat16*)feat, rows, dev_of(h), out, h->err);
+  mlp_infer_kernel<<<grid, kInferThreads, sizeof(InferSmem), st>>>((const __nv_bfloat16*)feat, rows, dev_of(h),
+                                                                  out, h->err);
   MCU(cudaGetLastError());
   return SIM_OK;
 }
@@ -700,7 +728,7 @@ extern "C" SimStatus mlp_forward_noalloc(const float* params, int32_t n_params, 
   d.b1 = params + kOffB1; d.b2 = params + kOffB2; d.w3 = params + kOffW3; d.b3 = params + kOffB3;
   const long long tiles = (rows + kTile - 1) / kTile;
   const int grid = (int)std::min<long long>(tiles, 2LL * sms);
-  mlp_infer_kernel<<<grid, 128, sizeof(InferSmem), st>>>((const __nv_bfloat16*)feat, rows, d, out, err);
+  mlp_infer_kernel<<<grid, kInferThreads, sizeof(InferSmem), st>>>((const __nv_bfloat16*)feat, rows, d, out, err);
   MCU(cudaGetLastError());
   int e = 0;
   MCU(cudaMemcpyAsync(&e, err, sizeof(int), cudaMemcpyDeviceToHost, st));

@@ -3,9 +3,12 @@ against the oracle.
 
 Tolerances: the kernels read bfloat16 operands (as the oracle emulates) and evaluate
 SiLU with the hardware tanh approximation (relative error ~2^-11 of tanh, i.e. an absolute
-error ~2.5e-4 |z| of silu(z)); accumulation is FP32 against the oracle's FP64.  Outputs:
-5e-3 of the output scale; gradients: 2e-2 of each block's largest entry against the
-bfloat16-emulating oracle, 6e-2 against the plain FP64 gradient (the bfloat16 bound).
+error ~2.5e-4 |z| of silu(z)); the inference kernel evaluates the first layer's SiLU in
+bfloat16 pairs (its result is rounded to bfloat16 for the second GEMM in any case: one
+to two bfloat16 units of the last place instead of half of one); accumulation is FP32
+against the oracle's FP64.  Outputs: 5e-3 of the output scale; gradients: 2e-2 of each
+block's largest entry against the bfloat16-emulating oracle, 6e-2 against the plain FP64
+gradient (the bfloat16 bound).
 """
 import numpy as np
 import pytest
