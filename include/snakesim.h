@@ -95,7 +95,9 @@ typedef struct {
   int32_t n_links;      /* soft links; nodes = n_links * seg_per_link + 1               */
   int32_t seg_per_link; /* segments per link (rigid connector at every link boundary)   */
   int32_t n_fixed;      /* leading nodes clamped in place (cantilever: 2)               */
-  int32_t reserved;
+  float mu_side;        /* > 0: anisotropic friction (the wheels and scales of Sec. V):   *
+                         * mu along the body, mu_side across it, friction pair limited *
+                         * to the ellipse of the body frame; 0: isotropic mu            */
   float L0;             /* segment rest length [m]                                       */
   float mass;           /* node mass [kg]                                                */
   float alpha_s;        /* stretch compliance [m/N]                                      */

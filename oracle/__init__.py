@@ -25,7 +25,7 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 
 PRM_FIELDS = ("L0", "mass", "alpha_s", "alpha_b", "gain", "tau_inf", "tau_def", "mu",
               "damping", "radius", "gait_amp", "gait_freq", "gait_lag", "gait_offset",
-              "gait_scale", "gait_alternate", "x0", "y0", "z0", "yaw0")
+              "gait_scale", "gait_alternate", "x0", "y0", "z0", "yaw0", "mu_side")
 NK = 6  # multiplier slots per node: stretch, yaw, pitch, contact, friction x, friction y
 _lib = None
 

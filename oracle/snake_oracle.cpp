@@ -99,7 +99,7 @@ template <class T> inline T dot(const V3<T>& a, const V3<T>& b) { return a.x * b
 // ---------------------------------------------------------------- layout
 enum { P_L0, P_MASS, P_ALPHA_S, P_ALPHA_B, P_GAIN, P_TAU_INF, P_TAU_DEF, P_MU, P_DAMP,
        P_RADIUS, P_AMP, P_FREQ, P_LAG, P_OFFSET, P_SCALE, P_ALT, P_X0, P_Y0, P_Z0, P_YAW0,
-       NPRM };
+       P_MU_SIDE, NPRM };
 enum { C_DT, C_NSUB, C_ITERS, C_TOL, C_OMEGA, C_GX, C_GY, C_GZ, C_CONTACT, C_WARM, C_BETA,
        C_LATENCY, C_KI, C_KD, C_TP, C_PS, C_LAW_DT, NCFG };
 // Row kinds; a node i owns one multiplier slot per kind: stretch (i, i+1), yaw and
@@ -112,6 +112,7 @@ struct Snake {
   int N, L, seg, nfix;
   T L0, mass, alpha_s, alpha_b, gain, tau_inf, tau_def, mu, damp, radius;
   double amp, freq, lag, offset, scale, alt;
+  double mu_side;  // > 0: anisotropic friction, mu along the body and mu_side across it
 };
 
 template <class T>
@@ -123,8 +124,35 @@ Snake<T> load_snake(const int* nl, const int* seg, const int* nfix, const double
   S.gain = p[P_GAIN]; S.tau_inf = p[P_TAU_INF]; S.tau_def = p[P_TAU_DEF]; S.mu = p[P_MU];
   S.damp = p[P_DAMP]; S.radius = p[P_RADIUS];
   S.amp = p[P_AMP]; S.freq = p[P_FREQ]; S.lag = p[P_LAG]; S.offset = p[P_OFFSET];
-  S.scale = p[P_SCALE]; S.alt = p[P_ALT];
+  S.scale = p[P_SCALE]; S.alt = p[P_ALT]; S.mu_side = p[P_MU_SIDE];
   return S;
+}
+
+// Anisotropic friction (the wheels and scales of Sec. V): at node i the friction pair is
+// limited to the ellipse (l_t / mu)^2 + (l_s / mu_side)^2 <= lambda_n^2 in the body frame
+// (t along the chain at the substep start, s = z x t), instead of the disc of radius
+// mu lambda_n.  Unit horizontal body tangent at node i from the substep-start positions.
+template <class T>
+void body_tangent(const std::vector<V3<T>>& XS, int N, int i, double& tx, double& ty) {
+  const int a = std::max(i - 1, 0), b = std::min(i + 1, N - 1);
+  const double ex = val(XS[b].x) - val(XS[a].x), ey = val(XS[b].y) - val(XS[a].y);
+  const double n = std::sqrt(ex * ex + ey * ey);
+  if (n > 0.0) { tx = ex / n; ty = ey / n; } else { tx = 1.0; ty = 0.0; }
+}
+
+// Projection of the pair (px, py) onto that ellipse with lambda_n = ln, radially in the
+// coordinates scaled by the two coefficients (with mu_side = mu the disc projection).
+template <class T>
+void project_ellipse(T& px, T& py, double tx, double ty, double mu_t, double mu_s, const T& ln) {
+  T a = px * tx + py * ty, b = py * tx - px * ty;  // along, across
+  T u = a / mu_t, v = b / mu_s;
+  const double r2 = val(u) * val(u) + val(v) * val(v);
+  if (r2 > val(ln) * val(ln)) {
+    if (val(ln) <= 0.0) { a = T(0.0); b = T(0.0); }
+    else { T sc = ln / sqrt(u * u + v * v); a = a * sc; b = b * sc; }
+  }
+  px = a * tx - b * ty;
+  py = a * ty + b * tx;
 }
 
 struct Cfg {
@@ -321,7 +349,7 @@ T row_wgrad2(Rows<T>& R, const std::vector<double>& w, int i, int k) {
 //    opposite to u, and forces lambda_t = 0 when lambda_n = 0 (Sec. IV, Coulomb cone).
 template <class T>
 double residual(const Snake<T>& S, const Cfg& C, Rows<T>& R, const std::vector<double>& w,
-                const std::vector<T>& lam) {
+                const std::vector<T>& lam, const std::vector<V3<T>>& XS) {
   double r = 0.0, L0 = val(S.L0);
   for (int i = 0; i < S.N; ++i) {
     for (int k = 0; k < NK; ++k) {
@@ -334,12 +362,18 @@ double residual(const Snake<T>& S, const Cfg& C, Rows<T>& R, const std::vector<d
         double b = w[i] * l;
         e = std::fabs(c + b - std::sqrt(c * c + b * b)) / L0;
       } else {  // friction pair of node i
-        double rho = w[i] * val(S.mu) * val(lam[i * NK + R_CONTACT]);
         double ax = w[i] * val(lam[i * NK + R_FX]), ay = w[i] * val(lam[i * NK + R_FY]);
         double px = ax - val(R.C(i, R_FX)), py = ay - val(R.C(i, R_FY));
-        double n = std::sqrt(px * px + py * py);
-        if (n > rho) {
-          if (rho > 0.0) { px *= rho / n; py *= rho / n; } else { px = 0.0; py = 0.0; }
+        if (S.mu_side > 0.0) {
+          double tx, ty;
+          body_tangent(XS, S.N, i, tx, ty);
+          project_ellipse(px, py, tx, ty, val(S.mu), S.mu_side, w[i] * val(lam[i * NK + R_CONTACT]));
+        } else {
+          double rho = w[i] * val(S.mu) * val(lam[i * NK + R_CONTACT]);
+          double n = std::sqrt(px * px + py * py);
+          if (n > rho) {
+            if (rho > 0.0) { px *= rho / n; py *= rho / n; } else { px = 0.0; py = 0.0; }
+          }
         }
         e = std::sqrt((ax - px) * (ax - px) + (ay - py) * (ay - py)) / L0;
       }
@@ -562,7 +596,7 @@ double snake_step(const Snake<T>& S, const Cfg& C, long long step_index, V3<T>* 
     int k = 0;
     for (;; ++k) {
       eval_rows(S, C, X, XS, theta, R);
-      double r = residual(S, C, R, w, lam);
+      double r = residual(S, C, R, w, lam, XS);
       if (r <= C.tol || k >= C.iters) { rmax = std::max(rmax, r); break; }
       // new multipliers from (x^k, lambda^k) only
       for (int i = 0; i < N; ++i) {
@@ -587,11 +621,17 @@ double snake_step(const Snake<T>& S, const Cfg& C, long long step_index, V3<T>* 
           int jx = i * NK + R_FX, jy = i * NK + R_FY;
           T tx = lam[jx] + C.omega * (-R.C(i, R_FX) / w[i]);
           T ty = lam[jy] + C.omega * (-R.C(i, R_FY) / w[i]);
-          T rad = S.mu * lam[i * NK + R_CONTACT];
-          double n2 = val(tx) * val(tx) + val(ty) * val(ty);
-          if (n2 > val(rad) * val(rad)) {
-            if (val(rad) <= 0.0) { tx = T(0.0); ty = T(0.0); }
-            else { T nrm = sqrt(tx * tx + ty * ty); tx = tx * rad / nrm; ty = ty * rad / nrm; }
+          if (S.mu_side > 0.0) {  // ellipse of the body frame
+            double bx, by;
+            body_tangent(XS, N, i, bx, by);
+            project_ellipse(tx, ty, bx, by, val(S.mu), S.mu_side, lam[i * NK + R_CONTACT]);
+          } else {
+            T rad = S.mu * lam[i * NK + R_CONTACT];
+            double n2 = val(tx) * val(tx) + val(ty) * val(ty);
+            if (n2 > val(rad) * val(rad)) {
+              if (val(rad) <= 0.0) { tx = T(0.0); ty = T(0.0); }
+              else { T nrm = sqrt(tx * tx + ty * ty); tx = tx * rad / nrm; ty = ty * rad / nrm; }
+            }
           }
           lnew[jx] = tx; lnew[jy] = ty;
         }

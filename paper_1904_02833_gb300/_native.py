@@ -33,7 +33,7 @@ SNAKE_FLOAT_FIELDS = ("L0", "mass", "alpha_s", "alpha_b", "gain", "tau_inf", "ta
 
 class SnakeParams(ctypes.Structure):
     _fields_ = ([("n_links", ctypes.c_int32), ("seg_per_link", ctypes.c_int32),
-                 ("n_fixed", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                 ("n_fixed", ctypes.c_int32), ("mu_side", ctypes.c_float)]
                 + [(f, ctypes.c_float) for f in SNAKE_FLOAT_FIELDS])
 
 

@@ -58,7 +58,7 @@ namespace {
 #endif
 // Persistent: every warp takes the next work item (32/G snakes of one node count) from
 // the layout's counter in global memory until none is left.
-template <int NPL, int G, bool SPLIT>
+template <int NPL, int G, bool SPLIT, bool ANISO>
 __global__ void __launch_bounds__(128, SNAKE_MIN_BLOCKS) snake_solver_kernel(SolverArgs A) {
   const int lane = threadIdx.x & 31;
   for (;;) {
@@ -70,19 +70,20 @@ __global__ void __launch_bounds__(128, SNAKE_MIN_BLOCKS) snake_solver_kernel(Sol
     const int gi = lane / G;
     const bool ok = gi < item.y;
     const int snake = ok ? A.order[item.x + gi] : 0;
-    run_group<NPL, G, SPLIT>(A, snake, ok);
+    run_group<NPL, G, SPLIT, ANISO>(A, snake, ok);
   }
 }
 
 typedef void (*SolverKernel)(SolverArgs);
 constexpr int kLayouts = 12;
-// [split][layout_id(G, NPL)]
-#define SNAKE_KERNELS(S)                                                                  \
-  {snake_solver_kernel<1, 8, S>,  snake_solver_kernel<2, 8, S>,  snake_solver_kernel<3, 8, S>,  \
-   snake_solver_kernel<4, 8, S>,  snake_solver_kernel<1, 16, S>, snake_solver_kernel<2, 16, S>, \
-   snake_solver_kernel<3, 16, S>, snake_solver_kernel<4, 16, S>, snake_solver_kernel<1, 32, S>, \
-   snake_solver_kernel<2, 32, S>, snake_solver_kernel<3, 32, S>, snake_solver_kernel<4, 32, S>}
-const SolverKernel kSolverKernels[2][kLayouts] = {SNAKE_KERNELS(false), SNAKE_KERNELS(true)};
+// [split][anisotropic friction][layout_id(G, NPL)]
+#define SNAKE_KERNELS(S, F)                                                                          \
+  {snake_solver_kernel<1, 8, S, F>,  snake_solver_kernel<2, 8, S, F>,  snake_solver_kernel<3, 8, S, F>,  \
+   snake_solver_kernel<4, 8, S, F>,  snake_solver_kernel<1, 16, S, F>, snake_solver_kernel<2, 16, S, F>, \
+   snake_solver_kernel<3, 16, S, F>, snake_solver_kernel<4, 16, S, F>, snake_solver_kernel<1, 32, S, F>, \
+   snake_solver_kernel<2, 32, S, F>, snake_solver_kernel<3, 32, S, F>, snake_solver_kernel<4, 32, S, F>}
+const SolverKernel kSolverKernels[2][2][kLayouts] = {{SNAKE_KERNELS(false, false), SNAKE_KERNELS(false, true)},
+                                                     {SNAKE_KERNELS(true, false), SNAKE_KERNELS(true, true)}};
 #undef SNAKE_KERNELS
 
 // ------------------------------------------------------------------ scheduling
@@ -219,6 +220,7 @@ struct SimHandle {
   int lay_first[kLayouts + 1] = {};  // items of layout l are [lay_first[l], lay_first[l + 1])
   int lay_grid[kLayouts] = {};
   int lay_launch[kLayouts] = {};      // layouts with work, most work first
+  int aniso = 0;                      // some snake has anisotropic friction
   int n_lay = 0;
   int* work = nullptr;                // [kLayouts] work-queue counters
   cudaStream_t side[kLayouts] = {};
@@ -352,7 +354,7 @@ SimStatus build_items(SimHandle* h, const std::map<int, int>* only_bucket = null
     h->lay_grid[l] = 0;
     if (cnt[l] == 0) continue;
     int per_sm = 0;
-    CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kSolverKernels[0][l], 128, 0));
+    CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kSolverKernels[0][h->aniso][l], 128, 0));
     const int need = (cnt[l] + 3) / 4;  // four warps per block
     h->lay_grid[l] = std::max(1, std::min(need, std::max(1, per_sm) * sms));
     h->lay_launch[h->n_lay++] = l;
@@ -469,7 +471,7 @@ SimStatus launch_args(SimHandle* h, const SolverArgs& A, cudaStream_t st) {
     cudaStream_t s = fork ? h->side[l] : st;
     if (fork) CU(cudaStreamWaitEvent(s, h->ev_split, 0));
     CU(cudaMemsetAsync(B.work, 0, sizeof(int), s));
-    kSolverKernels[A.split ? 1 : 0][l]<<<h->lay_grid[l], 128, 0, s>>>(B);
+    kSolverKernels[A.split ? 1 : 0][h->aniso][l]<<<h->lay_grid[l], 128, 0, s>>>(B);
     CU(cudaGetLastError());
     h->launches += 1;
     if (fork) {
@@ -499,8 +501,10 @@ SimStatus sim_create(const SimConfig* cfg, int n_snakes, const SnakeParams* para
     long long N = (long long)p.n_links * p.seg_per_link + 1;
     if (p.n_links < 1 || p.seg_per_link < 1 || p.n_fixed < 0 || p.n_fixed > N || !(p.L0 > 0.f) ||
         !(p.mass > 0.f) || !(p.alpha_s >= 0.f) || !(p.alpha_b >= 0.f) || !(p.tau_inf > 0.f) ||
-        !(p.tau_def > 0.f) || !(p.mu >= 0.f) || !(p.damping >= 0.f))
-      return fail(SIM_EINVAL, "invalid parameters of snake " + std::to_string(s));
+        !(p.tau_def > 0.f) || !(p.mu >= 0.f) || !(p.damping >= 0.f) || !(p.mu_side >= 0.f) ||
+        (p.mu_side > 0.f && !(p.mu > 0.f)))
+      return fail(SIM_EINVAL, "invalid parameters of snake " + std::to_string(s) +
+                              " (anisotropic friction needs mu > 0 and mu_side > 0)");
     if (N > 128) return fail(SIM_EINVAL, "snake " + std::to_string(s) + " has more than 128 nodes");
   }
   SimHandle* h = new SimHandle();
@@ -508,6 +512,7 @@ SimStatus sim_create(const SimConfig* cfg, int n_snakes, const SnakeParams* para
   h->n = n_snakes;
   h->stream = (cudaStream_t)stream;
   h->hprm.assign(params, params + n_snakes);
+  for (int s = 0; s < n_snakes; ++s) h->aniso |= params[s].mu_side > 0.f ? 1 : 0;
   h->node_off.resize(n_snakes + 1);
   h->link_off.resize(n_snakes + 1);
   h->node_off[0] = h->link_off[0] = 0;
@@ -933,6 +938,8 @@ SimStatus sim_calib_forward(SimHandle* h, const float* theta, int n_steps, int c
   if (h->cur_sub >= 0) return fail(SIM_EINVAL, "a split env-step is in progress (sim_split_finish)");
   if (h->cfg.latency != SIM_LATENCY_EXP)
     return fail(SIM_EINVAL, "calibration differentiates the first-order chamber model only");
+  for (const SnakeParams& p : h->hprm)
+    if (p.mu_side > 0.f) return fail(SIM_EINVAL, "calibration differentiates isotropic friction only");
   if (!h->calib) h->calib = calib_new();
   std::string err;
   SimStatus st = calib_forward(*h->calib, h->prm, h->node_off_d, h->link_off_d, h->n, h->max_nodes,

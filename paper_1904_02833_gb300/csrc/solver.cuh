@@ -106,7 +106,35 @@ __device__ __forceinline__ float group_max(float r) {
 struct SnakeK {
   int N, seg, nfix, L, nb, lb;
   float L0, inv_L0, inv_m, mass, at_s, at_b, mu, radius, gain, e_inf, e_def, damp_over_h;
+  float mu_side, inv_mu, inv_mu_side;  // mu_side > 0: anisotropic friction (body frame)
 };
+
+// Friction pair (px, py) limited to the Coulomb set of normal multiplier ln: the disc
+// |p| <= mu ln, or with anisotropic friction (the wheels and scales of Sec. V) the ellipse
+// (p_t / mu)^2 + (p_s / mu_side)^2 <= ln^2 in the body frame (t = (bx, by) along the chain,
+// s = z x t), projected radially in the coordinates scaled by the two coefficients.
+template <bool ANISO>
+__device__ __forceinline__ void friction_limit(const SnakeK& S, float bx, float by, float ln, float& px,
+                                               float& py) {
+  if (ANISO && S.mu_side > 0.f) {
+    float a = px * bx + py * by, b = py * bx - px * by;
+    const float u = a * S.inv_mu, v = b * S.inv_mu_side;
+    const float r2 = u * u + v * v;
+    if (r2 > ln * ln) {
+      const float sc = ln > 0.f ? ln * rsqrtf(r2) : 0.f;
+      a *= sc; b *= sc;
+    }
+    px = a * bx - b * by;
+    py = a * by + b * bx;
+  } else {
+    const float rad = S.mu * ln;
+    const float n2 = px * px + py * py;
+    if (n2 > rad * rad) {
+      if (rad > 0.f) { const float sc = rad * rsqrtf(n2); px *= sc; py *= sc; }
+      else { px = 0.f; py = 0.f; }
+    }
+  }
+}
 
 // One pass over the rows at the current positions and multipliers.
 //   WARM = false: Jacobi pass.  Evaluates every row at (x^k, lambda^k), returns the
@@ -115,7 +143,7 @@ struct SnakeK {
 //   WARM = true: warm-start pass.  Uses d_j = lambda_j (zeroing rows that do not exist
 //     or touch no free node) and applies it, so that M (x - x~) = J^T lambda.
 // `stop_at` returns the group's stop decision (residual <= tol or cap reached).
-template <int NPL, int G, bool WARM>
+template <int NPL, int G, bool WARM, bool ANISO>
 __device__ __forceinline__ float row_pass(const SnakeK& S, const SolverArgs& A, int q,
                                           bool live, int kiter, const float (&xs)[NPL][3],
                                           float (&dx)[NPL][3], const float (&xsl)[3],
@@ -246,32 +274,34 @@ __device__ __forceinline__ float row_pass(const SnakeK& S, const SolverArgs& A, 
       float dn, dx, dy;
       if (WARM) { dn = ln; dx = lam[j][4]; dy = lam[j][5]; }
       else {
-        // residuals: Fischer-Burmeister on (c_n, w lambda_n); natural map of the disc
+        // body tangent at the substep start (anisotropic friction only)
+        float bx = 1.f, by = 0.f;
+        if (ANISO && S.mu_side > 0.f) {
+          float ax0 = xs[j][0], ay0 = xs[j][1], bx0 = xs[j][0], by0 = xs[j][1];
+          if (i >= 1) { ax0 = (j > 0) ? xs[j - 1][0] : xsl[0]; ay0 = (j > 0) ? xs[j - 1][1] : xsl[1]; }
+          if (i + 1 <= S.N - 1) {
+            bx0 = (j + 1 < NPL) ? xs[j + 1][0] : xsr[0];
+            by0 = (j + 1 < NPL) ? xs[j + 1][1] : xsr[1];
+          }
+          const float ex = bx0 - ax0, ey = by0 - ay0, en2 = ex * ex + ey * ey;
+          if (en2 > 0.f) { const float ie = rsqrtf(en2); bx = ex * ie; by = ey * ie; }
+        }
+        // residuals: Fischer-Burmeister on (c_n, w lambda_n); natural map of the cone
         const float b = wi * ln;
         r = fmaxf(r, fabsf(cn + b - sqrtf(cn * cn + b * b)) * S.inv_L0);
-        const float rho = wi * S.mu * ln;
         const float ax = wi * lam[j][4], ay = wi * lam[j][5];
         float px = ax - ux, py = ay - uy;
-        const float pn2 = px * px + py * py;
-        if (pn2 > rho * rho) {
-          if (rho > 0.f) { const float sc1 = rho * rsqrtf(pn2); px *= sc1; py *= sc1; }
-          else { px = 0.f; py = 0.f; }
-        }
+        friction_limit<ANISO>(S, bx, by, wi * ln, px, py);
         // squared friction residual; one square root per pass for the whole lane
         q2 = fmaxf(q2, (ax - px) * (ax - px) + (ay - py) * (ay - py));
         // contact: lambda_n <- max(0, lambda_n + omega (-c_n / w))
         const float nl = fmaxf(0.f, ln - A.omega * cn * S.mass);
         dn = nl - ln;
-        // friction: relaxed update projected onto |lambda_t| <= mu lambda_n (current
-        // iterate's lambda_n)
+        // friction: relaxed update limited to the Coulomb set of the current iterate's
+        // lambda_n
         float tx = lam[j][4] - A.omega * ux * S.mass;
         float ty = lam[j][5] - A.omega * uy * S.mass;
-        const float rad = S.mu * ln;
-        const float n2 = tx * tx + ty * ty;
-        if (n2 > rad * rad) {
-          if (rad <= 0.f) { tx = 0.f; ty = 0.f; }
-          else { const float sc2 = rad * rsqrtf(n2); tx *= sc2; ty *= sc2; }
-        }
+        friction_limit<ANISO>(S, bx, by, ln, tx, ty);
         dx = tx - lam[j][4]; dy = ty - lam[j][5];
       }
       dl[j][3] = dn; dl[j][4] = dx; dl[j][5] = dy;
@@ -443,7 +473,9 @@ __device__ __forceinline__ float chamber_law(float p, float t, const SolverArgs&
 // filter, prediction), writes its features and leaves the state in HBM at that point
 // (positions = substep start, velocities = predicted), so that the warm-start network
 // can run between two launches.
-template <int NPL, int G, bool SPLIT>
+// ANISO: compiled with the anisotropic friction path (batches where some snake has
+// mu_side > 0); the isotropic kernels carry none of its code.
+template <int NPL, int G, bool SPLIT, bool ANISO>
 __device__ void run_group(const SolverArgs& A, int snake, bool valid) {
   const int lane = threadIdx.x & 31;
   const int q = lane & (G - 1);
@@ -460,6 +492,9 @@ __device__ void run_group(const SolverArgs& A, int snake, bool valid) {
   S.L0 = P.L0; S.inv_L0 = 1.0f / P.L0; S.inv_m = 1.0f / P.mass; S.mass = P.mass;
   S.at_s = P.alpha_s / (h * h); S.at_b = P.alpha_b / (h * h);
   S.mu = P.mu; S.radius = P.radius; S.gain = P.gain;
+  S.mu_side = P.mu_side > 0.f ? P.mu_side : 0.f;
+  S.inv_mu = S.mu_side > 0.f ? 1.0f / P.mu : 0.f;
+  S.inv_mu_side = S.mu_side > 0.f ? 1.0f / S.mu_side : 0.f;
   S.e_inf = expf(-h / P.tau_inf); S.e_def = expf(-h / P.tau_def);
   S.damp_over_h = expf(-P.damping * h) / h;
 
@@ -571,13 +606,13 @@ __device__ void run_group(const SolverArgs& A, int snake, bool valid) {
           lam[j][k] = l;
         }
       }
-      row_pass<NPL, G, true>(S, A, q, valid, 0, xs, dx, xsl, xsr, lam, th, stop);
+      row_pass<NPL, G, true, ANISO>(S, A, q, valid, 0, xs, dx, xsl, xsr, lam, th, stop);
     }
     bool done = !valid;
     float rs = 0.f;
     int ks = 0;
     for (int k = 0;; ++k) {
-      const float r = row_pass<NPL, G, false>(S, A, q, !done, k, xs, dx, xsl, xsr, lam, th, stop);
+      const float r = row_pass<NPL, G, false, ANISO>(S, A, q, !done, k, xs, dx, xsl, xsr, lam, th, stop);
       if (!done && stop) { done = true; rs = r; ks = k; }
       if (__all_sync(kFull, done)) break;
     }

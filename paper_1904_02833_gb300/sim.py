@@ -33,6 +33,7 @@ def make_params(w: dict):
         p.n_links = int(w["n_links"][i])
         p.seg_per_link = int(w["seg_per_link"][i])
         p.n_fixed = int(w["n_fixed"][i])
+        p.mu_side = float(w["mu_side"][i]) if "mu_side" in w else 0.0
         for f in N.SNAKE_FLOAT_FIELDS:
             setattr(p, f, float(w[f][i]))
     return arr

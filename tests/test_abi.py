@@ -36,7 +36,7 @@ def test_every_declared_symbol_is_exported(lib):
 def test_struct_layout_matches_header(tmp_path):
     from paper_1904_02833_gb300 import _native as N
     c = tmp_path / "sz.c"
-    fields = ["n_links", "n_fixed", "L0", "alpha_b", "gait_amp", "yaw0"]
+    fields = ["n_links", "n_fixed", "mu_side", "L0", "alpha_b", "gait_amp", "yaw0"]
     body = "\n".join('printf("%%zu\\n", offsetof(SnakeParams, %s));' % f for f in fields)
     c.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "snakesim.h"\nint main(void){'
                  'printf("%zu\\n%zu\\n", sizeof(SimConfig), sizeof(SnakeParams));'
@@ -69,6 +69,10 @@ def test_argument_validation_without_gpu(lib):
     bad = make_params(W.single_snake())
     bad[0].mass = 0.0
     assert lib.sim_create(ctypes.byref(cfg), 1, bad, None, ctypes.byref(h)) == N.SIM_EINVAL
+    aniso = make_params(W.single_snake())
+    aniso[0].mu_side = 1.0
+    aniso[0].mu = 0.0  # anisotropic friction needs a positive coefficient along the body
+    assert lib.sim_create(ctypes.byref(cfg), 1, aniso, None, ctypes.byref(h)) == N.SIM_EINVAL
     long = make_params(W.single_snake())
     long[0].n_links = 20  # 201 nodes > 128
     assert lib.sim_create(ctypes.byref(cfg), 1, long, None, ctypes.byref(h)) == N.SIM_EINVAL

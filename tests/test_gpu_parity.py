@@ -210,6 +210,18 @@ def test_chamber_law_matches_oracle(law_dt):
         compare(g, o)
 
 
+def test_anisotropic_friction_matches_oracle():
+    """Anisotropic friction (mu along the body, mu_side across it) on a ragged batch."""
+    w = W.batched(n=48, seed=37, links=(1, 8))
+    w["mu_side"] = w["mu"] * np.random.default_rng(3).uniform(1.5, 4.0, size=48)
+    s = W.solver_settings(iters=10)
+    g, o = Sim(w, s), oracle.OracleSim(w, s)
+    for _ in range(3):
+        g.step(2)
+        o.step(2)
+        compare(g, o)
+
+
 def test_graph_replay_is_bitwise_identical_to_direct_launch():
     w = ragged_batch()
     s = W.solver_settings(iters=10)

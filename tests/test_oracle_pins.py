@@ -382,6 +382,45 @@ def test_sliding_node_pair_stops_at_coulomb_distance():
     assert np.allclose(o.lam[:, 3], 0.01 * G * h * h, rtol=1e-9)
 
 
+def _slide(mu, mu_side, v0, axis):
+    w = one(W.pendulum(0.02), n_fixed=0, z0=0.01, mu=mu, mu_side=mu_side)
+    s = W.solver_settings(tol=1e-12, iters=20000)
+    o = oracle.OracleSim(w, s)
+    o.v[:, axis] = v0
+    o.step(20)  # 0.33 s: past the stop time v0 / (mu g) of every case below
+    return o, s["dt"] / s["n_sub"]
+
+
+def _coulomb_stop(mu, v0, h):
+    dist, v = 0.0, v0
+    while h * v > mu * G * h * h:
+        dist += h * v - mu * G * h * h
+        v -= mu * G * h
+    return dist
+
+
+def test_anisotropic_friction_along_and_across_the_body():
+    """Anisotropic friction (wheels / scales, Sec. V): the node pair of the sliding test
+    lies along x; sliding along its axis it stops after the Coulomb distance of mu, sliding
+    across it after that of mu_side; with mu_side = mu the trajectory is the isotropic one."""
+    mu, mu_side, v0 = 0.2, 0.7, 0.4
+    o, h = _slide(mu, mu_side, v0, 0)
+    assert np.allclose(o.x[:, 0] - [0.0, 0.02], _coulomb_stop(mu, v0, h), rtol=1e-7, atol=1e-12)
+    assert np.abs(o.x[:, 1]).max() < 1e-12
+    o, h = _slide(mu, mu_side, v0, 1)
+    assert np.allclose(o.x[:, 1], _coulomb_stop(mu_side, v0, h), rtol=1e-7, atol=1e-12)
+    assert np.allclose(o.x[:, 0], [0.0, 0.02], atol=1e-12)
+    w = W.batched(n=4, seed=8)
+    s = W.solver_settings(iters=40)
+    a = oracle.OracleSim(w, s)
+    w2 = {k: v.copy() for k, v in w.items()}
+    w2["mu_side"] = w2["mu"].copy()
+    b = oracle.OracleSim(w2, s)
+    a.step(4)
+    b.step(4)
+    assert np.abs(a.x - b.x).max() <= 1e-12 * np.abs(a.x).max()
+
+
 def test_calibration_gradient_matches_central_differences():
     """Forward-mode dual numbers through the oracle against central differences (step 1e-3
     relative) of the same loss, in a contact-free window with a fixed iteration count."""

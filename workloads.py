@@ -9,7 +9,7 @@ A workload is a dict of numpy arrays, one entry per snake:
   ints    : n_links, seg_per_link, n_fixed
   floats  : L0, mass, alpha_s, alpha_b, gain, tau_inf, tau_def, mu, damping, radius,
             gait_amp, gait_freq, gait_lag, gait_offset, gait_scale, gait_alternate,
-            x0, y0, z0, yaw0
+            x0, y0, z0, yaw0, mu_side (sideways friction coefficient; 0 = isotropic mu)
 
 and a dict of global solver settings (dt, n_sub, iters, tol, omega, gravity, contact,
 warm start, chamber model).
@@ -29,7 +29,7 @@ INT_FIELDS = ("n_links", "seg_per_link", "n_fixed")
 FLOAT_FIELDS = (
     "L0", "mass", "alpha_s", "alpha_b", "gain", "tau_inf", "tau_def", "mu",
     "damping", "radius", "gait_amp", "gait_freq", "gait_lag", "gait_offset",
-    "gait_scale", "gait_alternate", "x0", "y0", "z0", "yaw0",
+    "gait_scale", "gait_alternate", "x0", "y0", "z0", "yaw0", "mu_side",
 )
 
 # Physical defaults of the 1D-actuator snake (segment length, node mass, compliances,
@@ -38,7 +38,7 @@ DEFAULTS = dict(
     L0=0.02, mass=0.01, alpha_s=1e-8, alpha_b=1e-4, gain=20.0, tau_inf=0.15,
     tau_def=0.25, mu=0.5, damping=0.05, radius=0.01, gait_amp=1.0, gait_freq=1.0,
     gait_lag=math.pi / 2, gait_offset=0.0, gait_scale=1.0, gait_alternate=0.0,
-    x0=0.0, y0=0.0, z0=0.01, yaw0=0.0,
+    x0=0.0, y0=0.0, z0=0.01, yaw0=0.0, mu_side=0.0,
 )
 
 
