@@ -59,11 +59,13 @@ __device__ __forceinline__ float atan_any(float t) {
   if (a <= 1.f) return atan_unit(t);
   return copysignf(1.57079632679489662f - atan_unit(__frcp_rn(a)), t);
 }
-// atan2(y, x) for the bend angles: x > 0 (|angle| < 90 degrees, the normal case) takes the
-// polynomial; anything else falls back to atan2f.
+// atan2(y, x) for the bend angles from the same polynomial: x > 0 (|angle| < 90 degrees,
+// the normal case) directly, x < 0 shifted by +-pi, x = 0 at +-pi/2 (the library atan2f
+// would add a large body of code to every solver kernel for this rare branch).
 __device__ __forceinline__ float atan2_bend(float y, float x) {
   if (x > 0.f) return atan_any(__fdividef(y, x));
-  return atan2f(y, x);
+  if (x < 0.f) return atan_any(__fdividef(y, x)) + copysignf(3.14159265358979323846f, y);
+  return y > 0.f ? 1.57079632679489662f : (y < 0.f ? -1.57079632679489662f : 0.f);
 }
 
 struct Seg {  // derived quantities of the segment from node i to node i+1
@@ -551,7 +553,10 @@ __device__ void run_group(const SolverArgs& A, int snake, bool valid) {
         if (A.ucmd) {
           u = A.ucmd[S.lb + kl];
         } else {
-          float a = P.gait_offset + P.gait_scale * sinf(phase + (float)kl * P.gait_lag);
+          // argument reduced to [-pi, pi] first, where the fast sine is accurate to ~1e-6
+          float arg = phase + (float)kl * P.gait_lag;
+          arg -= 6.283185307179586f * rintf(arg * 0.15915494309189535f);
+          float a = P.gait_offset + P.gait_scale * __sinf(arg);
           a = fminf(1.f, fmaxf(-1.f, a)) * P.gait_amp;
           if (P.gait_alternate != 0.f && (kl & 1)) a = -a;
           u = a;
