@@ -36,6 +36,9 @@ SKIP = 0.5  # learned warm start: lambda0 = SKIP lambda_prev + m g h^2 network(f
 # 23, yaw 46, pitch 52, contact + friction 54, update 12; a division, square root or
 # transcendental counts as one operation).
 FLOP_PER_NODE_PASS = 216
+# DRAM bytes per row of the network kernel: ncu (80.80 MB read + 2.06 MB written) over a
+# 1,261,356-row launch of this build of mlp_infer_kernel
+MLP_DRAM_BYTES_PER_ROW = (80.799232e6 + 2.060544e6) / 1261356
 # Minimal HBM bytes of one launch per node (float4 position and velocity read + written,
 # six float multipliers read + written), per link (float2 pressures read + written) and
 # per snake (96-byte parameters, offsets, residual, update count, status).
@@ -304,6 +307,9 @@ def run_gpu(args):
                          "mlp": {"bound": "tensor", "achieved": mlp_tflops, "peak": bf16_peak,
                                  "unit": "TFLOP/s", "frac": mlp_tflops / bf16_peak,
                                  "ms_per_launch": mlp_ms, "rows": rows,
+                                 "traffic": MLP_DRAM_BYTES_PER_ROW * rows,
+                                 "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of "
+                                                   "one 1,261,356-row launch, scaled by rows",
                                  "peak_source": "MEASURED_PEAKS bf16_tflops (burst, of measured)"}},
             "e2e": {"value": e2e_value, "unit": "env-steps/s",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
