@@ -73,8 +73,8 @@ def pack_cfg(s: dict) -> np.ndarray:
     return np.array([s["dt"], s["n_sub"], s["iters"], s["tol"], s["omega"], g[0], g[1], g[2],
                      1.0 if s["contact"] else 0.0, s["warm"], s.get("beta", 1.0),
                      s.get("latency", 0), s.get("k_inflate", 0.23), s.get("k_deflate", 0.23),
-                     s.get("t_p", 0.085), s.get("p_source", 1.0), s.get("law_dt", 0.0083)],
-                    np.float64)
+                     s.get("t_p", 0.085), s.get("p_source", 1.0), s.get("law_dt", 0.0083),
+                     s.get("solver", 0), s.get("pcr_iters", 20)], np.float64)
 
 
 class OracleSim:
@@ -90,6 +90,8 @@ class OracleSim:
         self.prm = pack_params(w)
         self.cfg = pack_cfg(self.s)
         assert len(self.cfg) == lib().oracle_ncfg()
+        if self.s.get("solver", 0) == 1 and self.s["contact"]:
+            raise ValueError("the Newton + PCR solver covers contact-free substeps only")
         nn = self.nl.astype(np.int64) * self.seg + 1
         self.node_off = np.concatenate([[0], np.cumsum(nn)])
         self.link_off = np.concatenate([[0], np.cumsum(self.nl)])

@@ -101,7 +101,7 @@ enum { P_L0, P_MASS, P_ALPHA_S, P_ALPHA_B, P_GAIN, P_TAU_INF, P_TAU_DEF, P_MU, P
        P_RADIUS, P_AMP, P_FREQ, P_LAG, P_OFFSET, P_SCALE, P_ALT, P_X0, P_Y0, P_Z0, P_YAW0,
        P_MU_SIDE, NPRM };
 enum { C_DT, C_NSUB, C_ITERS, C_TOL, C_OMEGA, C_GX, C_GY, C_GZ, C_CONTACT, C_WARM, C_BETA,
-       C_LATENCY, C_KI, C_KD, C_TP, C_PS, C_LAW_DT, NCFG };
+       C_LATENCY, C_KI, C_KD, C_TP, C_PS, C_LAW_DT, C_SOLVER, C_PCR_ITERS, NCFG };
 // Row kinds; a node i owns one multiplier slot per kind: stretch (i, i+1), yaw and
 // pitch bend centred on i, contact of i, friction of i along world x and y.
 enum { R_STRETCH, R_YAW, R_PITCH, R_CONTACT, R_FX, R_FY, NK };
@@ -160,6 +160,7 @@ struct Cfg {
   int n_sub, iters, contact, warm;
   int latency, law_every;        // chamber model (0 exponential, 1 Sec. V-A law), its period
   double k_i, k_d, t_p, p_s;     // Sec. V-A law: gains, deflation threshold, source pressure
+  int solver, pcr_iters;         // 0 Jacobi; 1 Newton + preconditioned conjugate residual
 };
 Cfg load_cfg(const double* c) {
   Cfg C;
@@ -169,6 +170,7 @@ Cfg load_cfg(const double* c) {
   C.latency = (int)c[C_LATENCY]; C.k_i = c[C_KI]; C.k_d = c[C_KD]; C.t_p = c[C_TP]; C.p_s = c[C_PS];
   // the law's time step in whole substeps (at least one)
   C.law_every = std::max(1, (int)std::llround(c[C_LAW_DT] / C.h));
+  C.solver = (int)c[C_SOLVER]; C.pcr_iters = (int)c[C_PCR_ITERS];
   return C;
 }
 
@@ -407,6 +409,89 @@ void apply_rows(int N, Rows<T>& R, const std::vector<double>& w, const std::vect
   }
 }
 
+// ---------------------------------------------------------------- Newton + PCR
+// The paper's own solve of a step (Sec. IV-D): Newton iterations on the compliant rows,
+// each solving the Schur system of Eq. 8, (J M^-1 J^T + alpha~) dlambda = -(c + alpha~
+// lambda), approximately with a fixed number of preconditioned conjugate residual (PCR)
+// iterations with the diagonal (Jacobi) preconditioner, then lambda += dlambda and
+// x += M^-1 J^T dlambda.  Bilateral rows only (stretch, yaw, pitch): the contact and
+// friction rows of the paper's Fischer-Burmeister Newton are not part of this solver.
+// Counts matrix-vector products with J M^-1 J^T (one per PCR iteration plus one per
+// Newton step), stops when the normalised residual is <= tol or the count reaches `iters`.
+template <class T>
+int newton_pcr(const Snake<T>& S, const Cfg& C, std::vector<V3<T>>& X, const std::vector<V3<T>>& XS,
+               const std::vector<T>& theta, Rows<T>& R, const std::vector<double>& w, std::vector<T>& lam,
+               double& r_end) {
+  const int N = S.N, n = N * NK;
+  std::vector<T> D(n, T(1.0)), b(n, T(0.0)), x(n), z(n), p(n), q(n), Az(n);
+  std::vector<char> act(n, 0);
+  std::vector<V3<T>> U(N);
+  auto dot_act = [&](const std::vector<T>& a, const std::vector<T>& c) {
+    T s(0.0);
+    for (int j = 0; j < n; ++j) if (act[j]) s += a[j] * c[j];
+    return s;
+  };
+  // y = (J M^-1 J^T + alpha~) v on the active rows
+  auto matvec = [&](const std::vector<T>& v, std::vector<T>& y) {
+    for (int i = 0; i < N; ++i) U[i] = V3<T>{T(0.0), T(0.0), T(0.0)};
+    apply_rows(N, R, w, v, U);  // U = M^-1 J^T v
+    for (int i = 0; i < N; ++i)
+      for (int k = 0; k < NK; ++k) {
+        const int j = i * NK + k;
+        y[j] = T(0.0);
+        if (!act[j]) continue;
+        T a = alpha_tilde(S, C, k) * v[j];
+        for (int l = 0; l < row_nodes(k); ++l) a += dot(R.G(i, k, l), U[row_node(i, k, l)]);
+        y[j] = a;
+      }
+  };
+  int mv = 0;
+  for (;;) {
+    eval_rows(S, C, X, XS, theta, R);
+    r_end = residual(S, C, R, w, lam, XS);
+    if (r_end <= C.tol || mv >= C.iters) break;
+    for (int i = 0; i < N; ++i)
+      for (int k = 0; k < NK; ++k) {
+        const int j = i * NK + k;
+        act[j] = (k <= R_PITCH && R.ON(i, k) && val(row_wgrad2(R, w, i, k)) != 0.0) ? 1 : 0;
+        if (!act[j]) { D[j] = T(1.0); b[j] = T(0.0); continue; }
+        const T at = alpha_tilde(S, C, k);
+        D[j] = row_wgrad2(R, w, i, k) + at;
+        b[j] = -(R.C(i, k) + at * lam[j]);
+      }
+    // PCR from dlambda = 0: z = D^-1 r, p = z, q = A p
+    for (int j = 0; j < n; ++j) { x[j] = T(0.0); z[j] = act[j] ? b[j] / D[j] : T(0.0); p[j] = z[j]; }
+    matvec(z, Az);
+    ++mv;
+    for (int j = 0; j < n; ++j) q[j] = Az[j];
+    T zaz = dot_act(z, Az);
+    for (int it = 0; it < C.pcr_iters && mv < C.iters; ++it) {
+      T qs(0.0);
+      for (int j = 0; j < n; ++j) if (act[j]) qs += q[j] * q[j] / D[j];
+      if (!(val(qs) > 0.0)) break;
+      const T alpha = zaz / qs;
+      for (int j = 0; j < n; ++j) {
+        if (!act[j]) continue;
+        x[j] += alpha * p[j];
+        z[j] -= alpha * q[j] / D[j];
+      }
+      matvec(z, Az);
+      ++mv;
+      const T zaz_new = dot_act(z, Az);
+      const T beta = zaz_new / zaz;
+      zaz = zaz_new;
+      for (int j = 0; j < n; ++j) {
+        if (!act[j]) continue;
+        p[j] = z[j] + beta * p[j];
+        q[j] = Az[j] + beta * q[j];
+      }
+    }
+    for (int j = 0; j < n; ++j) if (act[j]) lam[j] += x[j];
+    apply_rows(N, R, w, x, X);  // x += M^-1 J^T dlambda at the linearisation point
+  }
+  return mv;
+}
+
 // ---------------------------------------------------------------- warm-start network
 // The learned warm start reads 24 features per constraint row at the predicted positions
 // of a substep and predicts the row's multiplier over m g h^2.  Row frame: horizontal
@@ -592,9 +677,14 @@ double snake_step(const Snake<T>& S, const Cfg& C, long long step_index, V3<T>* 
         }
       apply_rows(N, R, w, dl, X);
     }
+    if (C.solver == 1) {  // Newton + PCR instead of the Jacobi relaxation
+      double r = 0.0;
+      *iters += newton_pcr(S, C, X, XS, theta, R, w, lam, r);
+      rmax = std::max(rmax, r);
+    }
     // (a5/a6) Jacobi iterations.
     int k = 0;
-    for (;; ++k) {
+    for (; C.solver == 0; ++k) {
       eval_rows(S, C, X, XS, theta, R);
       double r = residual(S, C, R, w, lam, XS);
       if (r <= C.tol || k >= C.iters) { rmax = std::max(rmax, r); break; }
@@ -639,7 +729,7 @@ double snake_step(const Snake<T>& S, const Cfg& C, long long step_index, V3<T>* 
       for (size_t j = 0; j < lam.size(); ++j) { dl[j] = lnew[j] - lam[j]; lam[j] = lnew[j]; }
       apply_rows(N, R, w, dl, X);
     }
-    *iters += k;
+    if (C.solver == 0) *iters += k;
     // (a7) velocity from the substep displacement, exponential damping d [1/s].
     T damp = exp(-S.damp * h);
     for (int i = 0; i < N; ++i) {
