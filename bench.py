@@ -252,6 +252,8 @@ def run_gpu(args):
     h2d = int(sum(host[k].numel() * host[k].element_size() for k in inputs))
     d2h = int(sum(v.numel() * v.element_size() for v in host.values()))
 
+    solvers = None if args.no_solver_comparison else solver_comparison(args, flush, stream, local)
+
     if rank == 0:
         pk = peaks()
         L = results["learned"]
@@ -316,6 +318,8 @@ def run_gpu(args):
             "gpu_launches": int(L["launches"]),
             "clocks": clk_all.summary() if clk_all else None,
         }
+        if solvers is not None:
+            res["solver_comparison"] = solvers
         if world == 1 and not args.no_cpu_baseline:
             res["cpu_baseline"] = cpu_baseline(w, W.solver_settings(iters=CAP, tol=TOL, warm=W_COLD))
         print(json.dumps(res), flush=True)
@@ -326,6 +330,46 @@ def run_gpu(args):
 
 
 W_COLD = 0
+
+
+def solver_comparison(args, flush, stream, local, n=4096, steps=3):
+    """The Jacobi relaxation against the paper's Newton + PCR solve (Sec. IV-D; 20 PCR
+    iterations per Newton step), cold and from 0.5 x the previous multipliers, to the same
+    residual on a contact-free batch (the gait running, the snakes in free fall): time per
+    env-step and updates (Jacobi passes / matrix-vector products) per substep."""
+    import torch
+    from paper_1904_02833_gb300.sim import SnakeSim
+    w = W.batched(n=n, seed=7)
+    base = dict(iters=CAP, tol=TOL, contact=False)
+    sim = SnakeSim(w, W.solver_settings(**base))
+    for _ in range(args.warmup):
+        sim.step(1, graph=True)
+    sim.snapshot_save()
+    out = {"workload": "%d uneven snakes (2-8 links x 10 segments), contact off, residual %g, cap %d"
+                       % (n, TOL, CAP), "steps": steps}
+    for name, cfg in (("jacobi_cold", dict(solver=0, warm=0, beta=1.0)),
+                      ("jacobi_previous", dict(solver=0, warm=1, beta=0.5)),
+                      ("newton_pcr_cold", dict(solver=1, warm=0, beta=1.0)),
+                      ("newton_pcr_previous", dict(solver=1, warm=1, beta=0.5))):
+        sim.set_config(**cfg)
+        sim.snapshot_restore()
+        sim.step(1, graph=True)
+        sim.snapshot_restore()
+        ms, upd, rmax = [], [], 0.0
+        for _ in range(steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            sim.step(1, graph=True)
+            b.record(stream)
+            st = sim.state()
+            upd.append(float(st["iters"].double().mean()) / 20)
+            rmax = max(rmax, float(st["resid"].max()))
+            ms.append(a.elapsed_time(b))
+        out[name] = {"ms_per_step": float(np.mean(ms)), "env_steps_per_s": n * steps / (sum(ms) / 1e3),
+                     "updates_per_substep": round(float(np.mean(upd)), 2), "residual_max": rmax}
+    sim.close()
+    return out
 
 
 def cpu_baseline(w, s, n_sample=None, budget_s=20.0):
@@ -392,6 +436,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-solver-comparison", action="store_true",
+                    help="skip the Jacobi vs Newton + PCR leg (contact-free batch)")
     ap.add_argument("--save-net", default=None, help="write the trained network parameters (.npy)")
     ap.add_argument("--load-net", default=None, help="use saved network parameters instead of training")
     ap.add_argument("--snakes", type=int, default=N_SNAKES,

@@ -84,7 +84,16 @@ typedef struct {
   float t_p;          /* > 0; the paper's 0.68 psi of an 8 psi maximum = 0.085           */
   float p_source;     /* > 0; source pressure                                            */
   float law_dt;       /* >= 0 [s]; the paper's time step 0.0083 s                        */
+  int32_t solver;     /* SIM_SOLVER_*                                                    */
+  int32_t pcr_iters;  /* SIM_SOLVER_NEWTON_PCR: PCR iterations per Newton step (>= 1; the *
+                       * paper uses 20)                                                   */
 } SimConfig;
+
+/* Substep solvers: the Jacobi relaxation of Eq. 8 (`iters` caps its updates), or the
+ * paper's Newton steps with a preconditioned conjugate residual solve of the Schur system
+ * (Sec. IV-D) over the bilateral rows, for contact-free substeps only (`contact` = 0;
+ * `iters` caps the matrix-vector products; the update counts report them). */
+enum { SIM_SOLVER_JACOBI = 0, SIM_SOLVER_NEWTON_PCR = 1 };
 
 /* Chamber models: first-order latency with the per-snake tau_inf / tau_def (exact
  * exponential relaxation every substep), or the paper's discrete law (Sec. V-A). */

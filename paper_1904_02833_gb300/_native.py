@@ -23,7 +23,8 @@ class SimConfig(ctypes.Structure):
                 ("warm", ctypes.c_int32), ("beta", ctypes.c_float),
                 ("latency", ctypes.c_int32), ("k_inflate", ctypes.c_float),
                 ("k_deflate", ctypes.c_float), ("t_p", ctypes.c_float),
-                ("p_source", ctypes.c_float), ("law_dt", ctypes.c_float)]
+                ("p_source", ctypes.c_float), ("law_dt", ctypes.c_float),
+                ("solver", ctypes.c_int32), ("pcr_iters", ctypes.c_int32)]
 
 
 SNAKE_FLOAT_FIELDS = ("L0", "mass", "alpha_s", "alpha_b", "gain", "tau_inf", "tau_def", "mu",
@@ -38,7 +39,7 @@ class SnakeParams(ctypes.Structure):
 
 
 assert ctypes.sizeof(SnakeParams) == 96
-assert ctypes.sizeof(SimConfig) == 72
+assert ctypes.sizeof(SimConfig) == 80
 
 _lib = None
 P = ctypes.c_void_p

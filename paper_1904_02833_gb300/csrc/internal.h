@@ -53,6 +53,7 @@ struct SolverArgs {
   int latency;            // SIM_LATENCY_*
   int law_every;          // SIM_LATENCY_LAW: substeps per law step
   float k_i, k_d, t_p, p_s;
+  int pcr_iters;          // SIM_SOLVER_NEWTON_PCR: PCR iterations per Newton step
 };
 
 // Calibration (adjoint) state of a simulator, defined in adjoint.cu.

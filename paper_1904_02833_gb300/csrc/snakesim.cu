@@ -58,8 +58,9 @@ namespace {
 #endif
 // Persistent: every warp takes the next work item (32/G snakes of one node count) from
 // the layout's counter in global memory until none is left.
-template <int NPL, int G, bool SPLIT, bool ANISO>
+template <int NPL, int G, bool SPLIT, int VAR>
 __global__ void __launch_bounds__(128, SNAKE_MIN_BLOCKS) snake_solver_kernel(SolverArgs A) {
+  extern __shared__ float solver_smem[];  // Newton + PCR only (kPcrFloatsPerSlot x 32 NPL per warp)
   const int lane = threadIdx.x & 31;
   for (;;) {
     int it = 0;
@@ -70,20 +71,23 @@ __global__ void __launch_bounds__(128, SNAKE_MIN_BLOCKS) snake_solver_kernel(Sol
     const int gi = lane / G;
     const bool ok = gi < item.y;
     const int snake = ok ? A.order[item.x + gi] : 0;
-    run_group<NPL, G, SPLIT, ANISO>(A, snake, ok);
+    run_group<NPL, G, SPLIT, VAR>(A, snake, ok, solver_smem);
   }
 }
 
 typedef void (*SolverKernel)(SolverArgs);
 constexpr int kLayouts = 12;
-// [split][anisotropic friction][layout_id(G, NPL)]
+// [split][solver variant: kVarJacobi, kVarAniso, kVarPcr][layout_id(G, NPL)]
 #define SNAKE_KERNELS(S, F)                                                                          \
   {snake_solver_kernel<1, 8, S, F>,  snake_solver_kernel<2, 8, S, F>,  snake_solver_kernel<3, 8, S, F>,  \
    snake_solver_kernel<4, 8, S, F>,  snake_solver_kernel<1, 16, S, F>, snake_solver_kernel<2, 16, S, F>, \
    snake_solver_kernel<3, 16, S, F>, snake_solver_kernel<4, 16, S, F>, snake_solver_kernel<1, 32, S, F>, \
    snake_solver_kernel<2, 32, S, F>, snake_solver_kernel<3, 32, S, F>, snake_solver_kernel<4, 32, S, F>}
-const SolverKernel kSolverKernels[2][2][kLayouts] = {{SNAKE_KERNELS(false, false), SNAKE_KERNELS(false, true)},
-                                                     {SNAKE_KERNELS(true, false), SNAKE_KERNELS(true, true)}};
+const SolverKernel kSolverKernels[2][3][kLayouts] = {
+    {SNAKE_KERNELS(false, kVarJacobi), SNAKE_KERNELS(false, kVarAniso), SNAKE_KERNELS(false, kVarPcr)},
+    {SNAKE_KERNELS(true, kVarJacobi), SNAKE_KERNELS(true, kVarAniso), SNAKE_KERNELS(true, kVarPcr)}};
+// dynamic shared memory of a block of the Newton + PCR kernels
+inline size_t pcr_smem_bytes(int lay) { return (size_t)4 * kPcrFloatsPerSlot * 32 * layout_npl(lay) * sizeof(float); }
 #undef SNAKE_KERNELS
 
 // ------------------------------------------------------------------ scheduling
@@ -263,6 +267,10 @@ SimStatus validate_cfg(const SimConfig* c) {
       c->warm < 0 || c->warm > 2 || !(c->beta >= 0.f && c->beta <= 1.f))
     return fail(SIM_EINVAL, "invalid config (dt > 0, n_sub >= 1, iters >= 0, tol >= 0, omega > 0, "
                             "warm in 0..2, beta in [0, 1])");
+  if (c->solver != SIM_SOLVER_JACOBI && c->solver != SIM_SOLVER_NEWTON_PCR)
+    return fail(SIM_EINVAL, "invalid config: solver must be SIM_SOLVER_JACOBI or SIM_SOLVER_NEWTON_PCR");
+  if (c->solver == SIM_SOLVER_NEWTON_PCR && (c->contact != 0 || c->pcr_iters < 1))
+    return fail(SIM_EINVAL, "the Newton + PCR solver needs contact = 0 and pcr_iters >= 1");
   if (c->latency != SIM_LATENCY_EXP && c->latency != SIM_LATENCY_LAW)
     return fail(SIM_EINVAL, "invalid config: latency must be SIM_LATENCY_EXP or SIM_LATENCY_LAW");
   if (c->latency == SIM_LATENCY_LAW &&
@@ -281,6 +289,12 @@ int default_layout(int N) {
     }
   }
   return -1;
+}
+
+// Kernel variant of the handle's configuration and parameters.
+int solver_var(const SimHandle* h) {
+  if (h->cfg.solver == SIM_SOLVER_NEWTON_PCR) return kVarPcr;
+  return h->aniso ? kVarAniso : kVarJacobi;
 }
 
 SimStatus build_items(SimHandle* h, const std::map<int, int>* only_bucket = nullptr) {
@@ -354,7 +368,9 @@ SimStatus build_items(SimHandle* h, const std::map<int, int>* only_bucket = null
     h->lay_grid[l] = 0;
     if (cnt[l] == 0) continue;
     int per_sm = 0;
-    CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kSolverKernels[0][h->aniso][l], 128, 0));
+    const int var = solver_var(h);
+    CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kSolverKernels[0][var][l], 128,
+                                                     var == kVarPcr ? pcr_smem_bytes(l) : 0));
     const int need = (cnt[l] + 3) / 4;  // four warps per block
     h->lay_grid[l] = std::max(1, std::min(need, std::max(1, per_sm) * sms));
     h->lay_launch[h->n_lay++] = l;
@@ -393,6 +409,7 @@ SolverArgs make_args(SimHandle* h, int n_steps) {
   A.latency = h->cfg.latency;
   A.law_every = std::max(1, (int)std::llround((double)h->cfg.law_dt / A.h_d));
   A.k_i = h->cfg.k_inflate; A.k_d = h->cfg.k_deflate; A.t_p = h->cfg.t_p; A.p_s = h->cfg.p_source;
+  A.pcr_iters = h->cfg.pcr_iters;
   return A;
 }
 
@@ -471,7 +488,9 @@ SimStatus launch_args(SimHandle* h, const SolverArgs& A, cudaStream_t st) {
     cudaStream_t s = fork ? h->side[l] : st;
     if (fork) CU(cudaStreamWaitEvent(s, h->ev_split, 0));
     CU(cudaMemsetAsync(B.work, 0, sizeof(int), s));
-    kSolverKernels[A.split ? 1 : 0][h->aniso][l]<<<h->lay_grid[l], 128, 0, s>>>(B);
+    const int var = solver_var(h);
+    kSolverKernels[A.split ? 1 : 0][var][l]<<<h->lay_grid[l], 128, var == kVarPcr ? pcr_smem_bytes(l) : 0,
+                                              s>>>(B);
     CU(cudaGetLastError());
     h->launches += 1;
     if (fork) {
@@ -596,9 +615,10 @@ SimStatus sim_set_config(SimHandle* h, const SimConfig* cfg) {
   if (!h) return fail(SIM_EINVAL, "null handle");
   SimStatus st = validate_cfg(cfg);
   if (st != SIM_OK) return st;
+  const bool regrid = cfg->solver != h->cfg.solver;  // another kernel variant, other occupancy
   h->cfg = *cfg;
   h->graph_dirty = true;
-  return SIM_OK;
+  return regrid ? build_items(h) : SIM_OK;
 }
 
 SimStatus sim_set_pressure(SimHandle* h, const float* u, int is_device) {

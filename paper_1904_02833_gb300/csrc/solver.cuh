@@ -138,6 +138,12 @@ __device__ __forceinline__ void friction_limit(const SnakeK& S, float bx, float 
   }
 }
 
+}  // namespace snakesim
+
+#include "pcr.cuh"  // Newton + PCR building blocks (use SnakeK)
+
+namespace snakesim {
+
 // One pass over the rows at the current positions and multipliers.
 //   WARM = false: Jacobi pass.  Evaluates every row at (x^k, lambda^k), returns the
 //     group's normalised residual, and (unless `apply` comes back false) replaces
@@ -469,16 +475,175 @@ __device__ __forceinline__ float chamber_law(float p, float t, const SolverArgs&
   return p;
 }
 
+// Newton + PCR solve of one contact-free substep (see pcr.cuh) for the snake of this lane
+// group, from the current multipliers and displacements; returns the final normalised
+// residual and the number of matrix-vector products.
+template <int NPL, int G>
+__device__ void newton_pcr(const SnakeK& S, const SolverArgs& A, int q, bool valid,
+                           const float (&xs)[NPL][3], float (&dx)[NPL][3], float (&lam)[NPL][6],
+                           const float (&th)[NPL], float* smem, float& r_end, int& mv) {
+  const int lane = threadIdx.x & 31;
+  const PcrSmem M = pcr_smem(smem, NPL);
+  const int base = (lane / G) * G * NPL;
+  const float L0 = S.L0;
+  float x[NPL][3], z[NPL][3], p[NPL][3], qv[NPL][3], iD[NPL][3], y[NPL][3], u[NPL][3];
+  bool gdone = !valid;
+  mv = 0;
+  r_end = 0.f;
+  for (;;) {
+    // ---- linearise at x = x_s + d: segments, rows, preconditioner, right-hand side
+#pragma unroll
+    for (int j = 0; j < NPL; ++j)
+#pragma unroll
+      for (int d = 0; d < 3; ++d) { M.U(d, base + q * NPL + j) = xs[j][d]; M.U(3 + d, base + q * NPL + j) = dx[j][d]; }
+    __syncwarp();
+    float r = 0.f;
+    Seg sp = make_seg(1.f, 0.f, 0.f, L0);
+    {
+      const int i0 = q * NPL, s0 = base + i0;
+      if (valid && i0 >= 1 && i0 <= S.N - 1)
+        sp = make_seg((M.U(0, s0) - M.U(0, s0 - 1)) + (M.U(3, s0) - M.U(3, s0 - 1)),
+                      (M.U(1, s0) - M.U(1, s0 - 1)) + (M.U(4, s0) - M.U(4, s0 - 1)),
+                      (M.U(2, s0) - M.U(2, s0 - 1)) + (M.U(5, s0) - M.U(5, s0 - 1)), L0);
+    }
+#pragma unroll
+    for (int j = 0; j < NPL; ++j) {
+      const int i = q * NPL + j, s = base + i;
+      const bool act = valid && i < S.N;
+      const float wi = (i < S.nfix) ? 0.f : S.inv_m;
+      const float wl = (i - 1 < S.nfix) ? 0.f : S.inv_m;
+      const float wr = (i + 1 < S.nfix) ? 0.f : S.inv_m;
+      const bool has_seg = act && i + 1 <= S.N - 1;
+      Seg sc = make_seg(1.f, 0.f, 0.f, L0);
+      if (has_seg)
+        sc = make_seg((M.U(0, s + 1) - xs[j][0]) + (M.U(3, s + 1) - dx[j][0]),
+                      (M.U(1, s + 1) - xs[j][1]) + (M.U(4, s + 1) - dx[j][1]),
+                      (M.U(2, s + 1) - xs[j][2]) + (M.U(5, s + 1) - dx[j][2]), L0);
+      // segment i's gradients for the products (zero where there is no segment)
+      M.S(0, s) = has_seg ? sc.nx : 0.f; M.S(1, s) = has_seg ? sc.ny : 0.f; M.S(2, s) = has_seg ? sc.nz : 0.f;
+      M.S(3, s) = has_seg ? sc.gyx : 0.f; M.S(4, s) = has_seg ? sc.gyy : 0.f;
+      M.S(5, s) = has_seg ? sc.gpx : 0.f; M.S(6, s) = has_seg ? sc.gpy : 0.f; M.S(7, s) = has_seg ? sc.gpz : 0.f;
+      float b[3] = {0.f, 0.f, 0.f};
+      iD[j][0] = iD[j][1] = iD[j][2] = 0.f;
+      if (has_seg && wi + wr > 0.f) {  // stretch
+        const float c = sc.len - L0;
+        r = fmaxf(r, fabsf(c + S.at_s * lam[j][0]) * S.inv_L0);
+        iD[j][0] = 1.f / (wi + wr + S.at_s);
+        b[0] = -(c + S.at_s * lam[j][0]);
+      }
+      if (act && i >= 1 && i <= S.N - 2) {
+        {  // yaw
+          const float cz = sp.ex * sc.ey - sp.ey * sc.ex, dh = sp.ex * sc.ex + sp.ey * sc.ey;
+          const float c = L0 * (atan2_bend(cz, dh) - th[j]);
+          const float g1x = -sp.gyx - sc.gyx, g1y = -sp.gyy - sc.gyy;
+          const float wg = wl * (sp.gyx * sp.gyx + sp.gyy * sp.gyy) + wi * (g1x * g1x + g1y * g1y) +
+                           wr * (sc.gyx * sc.gyx + sc.gyy * sc.gyy);
+          if (wg > 0.f) {
+            r = fmaxf(r, fabsf(c + S.at_b * lam[j][1]) * S.inv_L0);
+            iD[j][1] = 1.f / (wg + S.at_b);
+            b[1] = -(c + S.at_b * lam[j][1]);
+          }
+        }
+        {  // pitch
+          const float c = L0 * (sc.beta - sp.beta);
+          const float g1x = -sp.gpx - sc.gpx, g1y = -sp.gpy - sc.gpy, g1z = -sp.gpz - sc.gpz;
+          const float wg = wl * (sp.gpx * sp.gpx + sp.gpy * sp.gpy + sp.gpz * sp.gpz) +
+                           wi * (g1x * g1x + g1y * g1y + g1z * g1z) +
+                           wr * (sc.gpx * sc.gpx + sc.gpy * sc.gpy + sc.gpz * sc.gpz);
+          if (wg > 0.f) {
+            r = fmaxf(r, fabsf(c + S.at_b * lam[j][2]) * S.inv_L0);
+            iD[j][2] = 1.f / (wg + S.at_b);
+            b[2] = -(c + S.at_b * lam[j][2]);
+          }
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < 3; ++k) { x[j][k] = 0.f; z[j][k] = b[k] * iD[j][k]; p[j][k] = z[j][k]; }
+      sp = sc;
+    }
+    if (!(r <= 3.0e38f)) r = INFINITY;
+    r = group_max<G>(r);
+    __syncwarp();
+    if (!gdone && (r <= A.tol || mv >= A.K)) { gdone = true; r_end = r; }
+    if (__all_sync(kFull, gdone)) break;
+    // ---- PCR on (J M^-1 J^T + alpha~) dlambda = b, diagonal preconditioner, from 0
+    pcr_matvec<NPL>(S, M, q, base, valid, iD, z, y, u);
+    if (!gdone) ++mv;
+    float zaz = 0.f;
+#pragma unroll
+    for (int j = 0; j < NPL; ++j)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) { qv[j][k] = y[j][k]; zaz += z[j][k] * y[j][k]; }
+    zaz = group_sum<G>(zaz);
+    bool on = !gdone;
+    for (int it = 0; it < A.pcr_iters; ++it) {
+      bool go = on && mv < A.K;
+      if (!__any_sync(kFull, go)) break;
+      float qs = 0.f;
+#pragma unroll
+      for (int j = 0; j < NPL; ++j)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) qs += qv[j][k] * qv[j][k] * iD[j][k];
+      qs = group_sum<G>(qs);
+      if (go && !(qs > 0.f)) { on = false; go = false; }
+      const float alpha = go ? zaz / qs : 0.f;
+#pragma unroll
+      for (int j = 0; j < NPL; ++j)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) { x[j][k] += alpha * p[j][k]; z[j][k] -= alpha * qv[j][k] * iD[j][k]; }
+      pcr_matvec<NPL>(S, M, q, base, valid, iD, z, y, u);
+      if (go) ++mv;
+      float zaz2 = 0.f;
+#pragma unroll
+      for (int j = 0; j < NPL; ++j)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) zaz2 += z[j][k] * y[j][k];
+      zaz2 = group_sum<G>(zaz2);
+      const float beta = (go && zaz != 0.f) ? zaz2 / zaz : 0.f;
+      if (go) zaz = zaz2;
+#pragma unroll
+      for (int j = 0; j < NPL; ++j)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          if (!go) continue;
+          p[j][k] = z[j][k] + beta * p[j][k];
+          qv[j][k] = y[j][k] + beta * qv[j][k];
+        }
+    }
+    // ---- lambda += dlambda, d += M^-1 J^T dlambda (gradients at the linearisation point)
+#pragma unroll
+    for (int j = 0; j < NPL; ++j)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) M.V(k, base + q * NPL + j) = x[j][k];
+    __syncwarp();
+    pcr_jt<NPL>(S, M, q, base, valid, u);
+    __syncwarp();
+    if (!gdone) {
+#pragma unroll
+      for (int j = 0; j < NPL; ++j) {
+        if (q * NPL + j >= S.N) continue;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) { lam[j][k] += x[j][k]; dx[j][k] += u[j][k]; }
+      }
+    }
+  }
+}
+
 // Advances the snake owned by this lane group.  Fused mode (A.split == 0): A.n_steps
 // env-steps with all substeps in registers.  Split mode: finishes substep A.sub (if >= 0)
 // of the current env-step and, if A.sub + 1 < n_sub, begins substep A.sub + 1 (gait,
 // filter, prediction), writes its features and leaves the state in HBM at that point
 // (positions = substep start, velocities = predicted), so that the warm-start network
 // can run between two launches.
-// ANISO: compiled with the anisotropic friction path (batches where some snake has
-// mu_side > 0); the isotropic kernels carry none of its code.
-template <int NPL, int G, bool SPLIT, bool ANISO>
-__device__ void run_group(const SolverArgs& A, int snake, bool valid) {
+// VAR: which solve the kernel carries.  kVarJacobi: the Jacobi relaxation with isotropic
+// friction; kVarAniso: the same with the anisotropic friction path (batches where some
+// snake has mu_side > 0; the other kernels carry none of its code); kVarPcr: Newton +
+// preconditioned conjugate residual over the bilateral rows (contact-free substeps;
+// `smem` is its per-block shared-memory area).
+enum { kVarJacobi = 0, kVarAniso = 1, kVarPcr = 2 };
+template <int NPL, int G, bool SPLIT, int VAR>
+__device__ void run_group(const SolverArgs& A, int snake, bool valid, float* smem) {
+  constexpr bool ANISO = VAR == kVarAniso;
   const int lane = threadIdx.x & 31;
   const int q = lane & (G - 1);
   SnakeK S;
@@ -616,10 +781,14 @@ __device__ void run_group(const SolverArgs& A, int snake, bool valid) {
     bool done = !valid;
     float rs = 0.f;
     int ks = 0;
-    for (int k = 0;; ++k) {
-      const float r = row_pass<NPL, G, false, ANISO>(S, A, q, !done, k, xs, dx, xsl, xsr, lam, th, stop);
-      if (!done && stop) { done = true; rs = r; ks = k; }
-      if (__all_sync(kFull, done)) break;
+    if (VAR == kVarPcr) {
+      newton_pcr<NPL, G>(S, A, q, valid, xs, dx, lam, th, smem, rs, ks);
+    } else {
+      for (int k = 0;; ++k) {
+        const float r = row_pass<NPL, G, false, ANISO>(S, A, q, !done, k, xs, dx, xsl, xsr, lam, th, stop);
+        if (!done && stop) { done = true; rs = r; ks = k; }
+        if (__all_sync(kFull, done)) break;
+      }
     }
     // a non-finite displacement anywhere in the snake marks the step (fmaxf drops NaN)
     float bad = 0.f;

@@ -57,6 +57,8 @@ def make_config(s: dict) -> N.SimConfig:
     c.t_p = float(s.get("t_p", 0.085))
     c.p_source = float(s.get("p_source", 1.0))
     c.law_dt = float(s.get("law_dt", 0.0083))
+    c.solver = int(s.get("solver", 0))
+    c.pcr_iters = int(s.get("pcr_iters", 20))
     return c
 
 

@@ -222,6 +222,35 @@ def test_anisotropic_friction_matches_oracle():
         compare(g, o)
 
 
+@pytest.mark.parametrize("tol,iters", [(0.0, 63), (1e-5, 5000)])
+def test_newton_pcr_matches_oracle(tol, iters):
+    """Newton + PCR (Sec. IV-D) on contact-free ragged snakes in free fall with the gait
+    running: three Newton steps of 20 PCR iterations (63 products per substep), and to
+    residual 1e-5, GPU against the oracle (states and product counts)."""
+    w = W.batched(n=40, seed=38, links=(1, 8))
+    s = W.solver_settings(iters=iters, tol=tol, contact=False, solver=1, pcr_iters=20)
+    g, o = Sim(w, s), oracle.OracleSim(w, s)
+    for _ in range(2):
+        g.step(1)
+        o.step(1)
+        # to a tolerance, FP32 and FP64 may stop a substep one Newton step apart; where x
+        # ends depends on the path by a second-order term (~1e-6 m here), i.e. ~1e-3 m/s
+        compare(g, o, vel_abs=1.2e-3 if tol == 0.0 else 5e-3)
+    st = g.state_host()
+    if tol == 0.0:
+        assert (st["iters"] == 20 * 63).all() and (o.iters == 20 * 63).all()
+    else:
+        assert (st["resid"] <= tol).all()
+        # counts move in whole Newton steps (21 products): within 10 % or two steps per env-step
+        assert (np.abs(st["iters"] - o.iters) <= np.maximum(0.1 * o.iters, 42)).all(), (st["iters"], o.iters)
+
+
+def test_newton_pcr_is_rejected_with_contact():
+    s = W.solver_settings(solver=1, contact=True)
+    with pytest.raises(Exception):
+        Sim(W.single_snake(), s)
+
+
 def test_graph_replay_is_bitwise_identical_to_direct_launch():
     w = ragged_batch()
     s = W.solver_settings(iters=10)
