@@ -152,7 +152,7 @@ def run_gpu(args):
         from paper_1904_02833_gb300.mlp import WarmStartMLP
         net, record = WarmStartMLP(np.load(args.load_net)), [{"loaded": args.load_net}]
     else:
-        net, record = train_warm_start(n_snakes=1024, rounds=2, skip=SKIP)
+        net, record = train_warm_start(n_snakes=2048, rounds=2, skip=SKIP)
     if args.save_net:
         np.save(args.save_net, net.params())
     t_train = time.perf_counter() - t_train
