@@ -245,6 +245,53 @@ def test_newton_pcr_matches_oracle(tol, iters):
         assert (np.abs(st["iters"] - o.iters) <= np.maximum(0.1 * o.iters, 42)).all(), (st["iters"], o.iters)
 
 
+def test_newton_pcr_with_learned_warm_start_matches_oracle():
+    """Newton + PCR behind the learned warm start (split stepping with the network between
+    launches), same network parameters on both sides, fixed product count."""
+    from oracle import mlp_oracle as M
+    from paper_1904_02833_gb300.mlp import WarmStartMLP
+    w = W.batched(n=24, seed=39, links=(1, 8))
+    s = W.solver_settings(iters=42, contact=False, solver=1, pcr_iters=20, warm=1, beta=0.5)
+    g, o = Sim(w, s), oracle.OracleSim(w, s)
+    g.step(1)
+    o.step(1)
+    p = M.init_params(10) * 0.5
+    net = WarmStartMLP(p)
+    g.set_mlp(net)
+    g.set_config(warm=2)
+    o.set_cfg(warm=2)
+    g.step(1)
+    o.step(1, mlp=p)
+    # the network's outputs agree to ~5e-3 of their scale (bfloat16 operands, hardware
+    # tanh); after two Newton steps the end state still depends on that start, and the
+    # velocity is the substep displacement over h
+    compare(g, o, vel_abs=5e-3)
+
+
+def test_autotune_keeps_the_state_and_the_physics():
+    """sim_autotune times every admissible lane layout per node count from a saved state
+    and restores it: the state and the step index are unchanged, the chosen layouts are
+    admissible, and stepping afterwards still matches the oracle."""
+    w = W.batched(n=64, seed=40, links=(1, 8))
+    s = W.solver_settings(iters=10)
+    g, o = Sim(w, s), oracle.OracleSim(w, s)
+    g.step(1)
+    o.step(1)
+    before = g.state_host()
+    k0 = g.step_index
+    g.autotune(1)
+    after = g.state_host()
+    for k in ("pos", "vel", "press"):
+        assert np.array_equal(before[k], after[k]), k
+    assert g.step_index == k0
+    for N in np.unique(W.n_nodes(w)):
+        G, npl = g.layout(int(N))
+        assert G in (8, 16, 32) and 1 <= npl <= 4 and G * npl >= N
+    g.step(2)
+    o.step(2)
+    compare(g, o)
+
+
 def test_newton_pcr_is_rejected_with_contact():
     s = W.solver_settings(solver=1, contact=True)
     with pytest.raises(Exception):
