@@ -253,6 +253,7 @@ def run_gpu(args):
     d2h = int(sum(v.numel() * v.element_size() for v in host.values()))
 
     solvers = None if args.no_solver_comparison else solver_comparison(args, flush, stream, local)
+    calib = None if args.no_calibration else calibration_leg(stream)
 
     if rank == 0:
         pk = peaks()
@@ -320,6 +321,8 @@ def run_gpu(args):
         }
         if solvers is not None:
             res["solver_comparison"] = solvers
+        if calib is not None:
+            res["calibration"] = calib
         if world == 1 and not args.no_cpu_baseline:
             res["cpu_baseline"] = cpu_baseline(w, W.solver_settings(iters=CAP, tol=TOL, warm=W_COLD))
         print(json.dumps(res), flush=True)
@@ -369,6 +372,48 @@ def solver_comparison(args, flush, stream, local, n=4096, steps=3):
         out[name] = {"ms_per_step": float(np.mean(ms)), "env_steps_per_s": n * steps / (sum(ms) / 1e3),
                      "updates_per_substep": round(float(np.mean(upd)), 2), "residual_max": rmax}
     sim.close()
+    return out
+
+
+def calibration_leg(stream, n=1024, steps=200, ckpt=20):
+    """The differentiable calibration rollout: 1024 four-link snakes, 200 env-steps of 20
+    substeps with 10 Jacobi updates each, checkpoints every 20 env-steps; the forward
+    rollout and the adjoint (backward) pass of a mean squared tip-trajectory loss against
+    a ground-truth rollout, timed with CUDA events."""
+    import torch
+    from paper_1904_02833_gb300.calib import rollout, theta_of
+    from paper_1904_02833_gb300.sim import SnakeSim
+    truth, guess = W.calibration(n=n, seed=5)
+    s = W.solver_settings(iters=10)
+    gt = SnakeSim(truth, s)
+    gt.step(1)
+    with torch.no_grad():
+        target = rollout(gt, theta_of(truth).cuda(), steps, ckpt)
+    sim = SnakeSim(guess, s)
+    sim.step(1)
+    sim.snapshot_save()
+    th = theta_of(guess).cuda().requires_grad_(True)
+    rollout(sim, th, 2, ckpt).sum().backward()  # warm-up (allocations, first launches)
+    sim.snapshot_restore()
+    th.grad = None
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    e[0].record(stream)
+    tips = rollout(sim, th, steps, ckpt)
+    loss = ((tips - target) ** 2).sum(-1).mean(0).sum()
+    e[1].record(stream)
+    loss.backward()
+    e[2].record(stream)
+    torch.cuda.synchronize()
+    fwd, bwd = e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2])
+    g = th.grad
+    out = {"workload": "%d snakes x 41 nodes, %d env-steps x 20 substeps x 10 updates, checkpoints every %d"
+                       % (n, steps, ckpt),
+           "forward_ms": fwd, "backward_ms": bwd,
+           "env_steps_per_s_forward": n * steps / (fwd / 1e3),
+           "env_steps_per_s_forward_backward": n * steps / ((fwd + bwd) / 1e3),
+           "gradient_finite": bool(torch.isfinite(g).all().item()), "loss": float(loss.item())}
+    sim.close()
+    gt.close()
     return out
 
 
@@ -438,6 +483,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-solver-comparison", action="store_true",
                     help="skip the Jacobi vs Newton + PCR leg (contact-free batch)")
+    ap.add_argument("--no-calibration", action="store_true",
+                    help="skip the differentiable calibration leg (forward + adjoint)")
     ap.add_argument("--save-net", default=None, help="write the trained network parameters (.npy)")
     ap.add_argument("--load-net", default=None, help="use saved network parameters instead of training")
     ap.add_argument("--snakes", type=int, default=N_SNAKES,
