@@ -39,6 +39,10 @@ FLOP_PER_NODE_PASS = 216
 # DRAM bytes per row of the network kernel: ncu (80.80 MB read + 2.06 MB written) over a
 # 1,261,356-row launch of this build of mlp_infer_kernel
 MLP_DRAM_BYTES_PER_ROW = (80.799232e6 + 2.060544e6) / 1261356
+# DRAM bytes per node of a split-mode launch of the 32-lane x 3-node solver kernel: ncu
+# (8.367616 MB read + 1.185536 MB written) over the 93,177 nodes that layout owns in the
+# 4096-snake batch (the features it writes are consumed from L2 by the network)
+SPLIT_DRAM_BYTES_PER_NODE = (8.367616e6 + 1.185536e6) / 93177
 # Minimal HBM bytes of one launch per node (float4 position and velocity read + written,
 # six float multipliers read + written), per link (float2 pressures read + written) and
 # per snake (96-byte parameters, offsets, residual, update count, status).
@@ -252,6 +256,25 @@ def run_gpu(args):
     h2d = int(sum(host[k].numel() * host[k].element_size() for k in inputs))
     d2h = int(sum(v.numel() * v.element_size() for v in host.values()))
 
+    # per-layout kernel times of the learned step (direct launches with an event pair
+    # around every solver kernel, on the stream it is launched on), for the roofline of
+    # the dominant kernel
+    sim.set_config(warm=2, beta=SKIP)
+    sim.snapshot_restore()
+    sim.step(1)
+    sim.kernel_times()
+    sim.kernel_timing(True)
+    kflop = {}
+    for _ in range(2):
+        sim.step(1)
+        its = sim.state()["iters"].double().cpu().numpy()
+        for N in np.unique(n_nodes_snake):
+            lay = sim.layout(int(N))
+            sel = n_nodes_snake == N
+            kflop[lay] = kflop.get(lay, 0.0) + FLOP_PER_NODE_PASS * float(((its[sel] + 20) * N).sum())
+    ktimes = sim.kernel_times()
+    sim.kernel_timing(False)
+
     solvers = None if args.no_solver_comparison else solver_comparison(args, flush, stream, local)
     calib = None if args.no_calibration else calibration_leg(stream)
 
@@ -263,7 +286,17 @@ def run_gpu(args):
         # solver family in the learned mode: Jacobi passes per step x 216 FLOP / time
         # (the network's share of the step is taken out with its own measured time)
         solver_time = L["t_local"] / args.steps - 20 * mlp_ms / 1e3
-        achieved = FLOP_PER_NODE_PASS * L["passes"] / args.steps / solver_time / 1e12
+        family = FLOP_PER_NODE_PASS * L["passes"] / args.steps / solver_time / 1e12
+        # the dominant kernel: the lane layout with the most kernel time in the learned step
+        dom = max(ktimes, key=lambda k: ktimes[k][0])
+        dom_ms, dom_n = ktimes[dom]
+        achieved = kflop.get(dom, 0.0) / (dom_ms / 1e3) / 1e12
+        dom_nodes = int(sum(int(N) * int((n_nodes_snake == N).sum()) for N in np.unique(n_nodes_snake)
+                            if sim.layout(int(N)) == dom))
+        traffic = SPLIT_DRAM_BYTES_PER_NODE * dom_nodes if dom == (32, 3) else None
+        per_layout = {"%dx%d" % k: {"ms_per_launch": v[0] / v[1], "launches": v[1],
+                                    "tflops": kflop.get(k, 0.0) / (v[0] / 1e3) / 1e12}
+                      for k, v in sorted(ktimes.items())}
         bytes_step = (BYTES_PER_NODE * total_nodes + BYTES_PER_LINK * total_links
                       + BYTES_PER_SNAKE * N_SNAKES)
         mlp_flop_row = 2 * (24 * 128 + 128 * 128 + 128)
@@ -302,8 +335,17 @@ def run_gpu(args):
                        "parallelism": "independent snakes per GPU (dp%d)" % world,
                        "training": {"seconds": round(t_train, 1), "rounds": record}},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
-                         "frac": achieved / alu_peak, "traffic": None,
-                         "kernel": "snake_solver_kernel<NPL, split> (learned mode)",
+                         "frac": achieved / alu_peak, "traffic": traffic,
+                         "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one "
+                                           "launch on the 4096-snake batch, scaled by the layout's nodes",
+                         "kernel": "snake_solver_kernel<%d, %d, 1, 0> (learned mode, %d lanes x %d nodes "
+                                   "per lane)" % (dom[1], dom[0], dom[0], dom[1]),
+                         "ms_per_launch": dom_ms / dom_n,
+                         "flop_per_node_pass": FLOP_PER_NODE_PASS,
+                         "solver_family": {"achieved": family, "frac": family / alu_peak,
+                                           "note": "all layout kernels of the learned step, step time "
+                                                   "minus the network's"},
+                         "per_layout": per_layout,
                          "peak_source": "152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz",
                          "hbm": {"algorithmic_bytes_per_launch": bytes_step,
                                  "peak_gbs": pk.get("hbm_gbs")},

@@ -234,6 +234,16 @@ SimStatus sim_calib_backward(SimHandle* h, const float* tips_bar, float* grad_th
 /* Kernel launches made by this handle so far (the count the benchmark reports). */
 SimStatus sim_launch_count(SimHandle* h, int64_t* launches);
 
+/* Per-layout kernel timing.  sim_kernel_timing(h, 1) makes the following sim_step /
+ * sim_split_* calls (not sim_step_graph) launch the layouts' solver kernels one after
+ * another on the handle's stream (instead of overlapping them on forked streams) with a
+ * CUDA event pair around every launch; sim_kernel_times synchronises the handle's stream and
+ * returns, per lane layout id (lanes 8/16/32 x nodes per lane 1..4: id = 4 (lanes / 16,
+ * i.e. 0, 1, 2) + nodes per lane - 1), the summed kernel time in ms and the launch count
+ * (host arrays of 12), then forgets the recorded launches.  Errors: SIM_EINVAL, SIM_ECUDA. */
+SimStatus sim_kernel_timing(SimHandle* h, int enable);
+SimStatus sim_kernel_times(SimHandle* h, float* ms, int64_t* launches);
+
 /* Frees the handle and its device buffers (synchronises the stream).  NULL is ok. */
 SimStatus sim_destroy(SimHandle* h);
 

@@ -66,6 +66,8 @@ SIGNATURES = {
     "sim_get_layout": [H, ctypes.c_int, I32P, I32P],
     "sim_set_layout": [H, ctypes.c_int, ctypes.c_int, ctypes.c_int],
     "sim_launch_count": [H, I64P],
+    "sim_kernel_timing": [H, ctypes.c_int],
+    "sim_kernel_times": [H, P, P],
     "sim_destroy": [H],
     "sim_set_mlp": [H, H],
     "sim_snapshot_save": [H],

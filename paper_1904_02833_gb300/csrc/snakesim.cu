@@ -227,6 +227,9 @@ struct SimHandle {
   int aniso = 0;                      // some snake has anisotropic friction
   int n_lay = 0;
   int* work = nullptr;                // [kLayouts] work-queue counters
+  bool timing = false;                // record an event pair around every solver launch
+  struct Timed { int lay; cudaEvent_t a, b; };
+  std::vector<Timed> timed;
   cudaStream_t side[kLayouts] = {};
   cudaEvent_t ev_side[kLayouts] = {};
   cudaEvent_t ev_split = nullptr;
@@ -477,7 +480,9 @@ SimStatus launch_steps(SimHandle* h, int n_steps, cudaStream_t st) {
 
 SimStatus launch_args(SimHandle* h, const SolverArgs& A, cudaStream_t st) {
   if (h->n_items == 0) return SIM_OK;
-  const bool fork = h->n_lay > 1;
+  // with kernel timing on, the layouts run one after another so that each event pair
+  // brackets one kernel alone
+  const bool fork = h->n_lay > 1 && !h->timing;
   if (fork) CU(cudaEventRecord(h->ev_split, st));
   for (int k = 0; k < h->n_lay; ++k) {
     const int l = h->lay_launch[k];
@@ -488,10 +493,23 @@ SimStatus launch_args(SimHandle* h, const SolverArgs& A, cudaStream_t st) {
     cudaStream_t s = fork ? h->side[l] : st;
     if (fork) CU(cudaStreamWaitEvent(s, h->ev_split, 0));
     CU(cudaMemsetAsync(B.work, 0, sizeof(int), s));
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    CU(cudaStreamIsCapturing(s, &cap));
+    const bool timed = h->timing && cap == cudaStreamCaptureStatusNone;
+    SimHandle::Timed tm{l, nullptr, nullptr};
+    if (timed) {
+      CU(cudaEventCreate(&tm.a));
+      CU(cudaEventCreate(&tm.b));
+      CU(cudaEventRecord(tm.a, s));
+    }
     const int var = solver_var(h);
     kSolverKernels[A.split ? 1 : 0][var][l]<<<h->lay_grid[l], 128, var == kVarPcr ? pcr_smem_bytes(l) : 0,
                                               s>>>(B);
     CU(cudaGetLastError());
+    if (timed) {
+      CU(cudaEventRecord(tm.b, s));
+      h->timed.push_back(tm);
+    }
     h->launches += 1;
     if (fork) {
       CU(cudaEventRecord(h->ev_side[l], s));
@@ -990,9 +1008,33 @@ SimStatus sim_launch_count(SimHandle* h, int64_t* launches) {
   return SIM_OK;
 }
 
+SimStatus sim_kernel_timing(SimHandle* h, int enable) {
+  if (!h) return fail(SIM_EINVAL, "null handle");
+  h->timing = enable != 0;
+  return SIM_OK;
+}
+
+SimStatus sim_kernel_times(SimHandle* h, float* ms, int64_t* launches) {
+  if (!h || !ms || !launches) return fail(SIM_EINVAL, "null handle or output");
+  for (int l = 0; l < kLayouts; ++l) { ms[l] = 0.f; launches[l] = 0; }
+  CU(cudaStreamSynchronize(h->stream));
+  SimStatus st = SIM_OK;
+  for (auto& t : h->timed) {
+    float e = 0.f;
+    if (st == SIM_OK && cudaEventElapsedTime(&e, t.a, t.b) != cudaSuccess) st = fail(SIM_ECUDA, "event timing");
+    ms[t.lay] += e;
+    launches[t.lay] += 1;
+    cudaEventDestroy(t.a);
+    cudaEventDestroy(t.b);
+  }
+  h->timed.clear();
+  return st;
+}
+
 SimStatus sim_destroy(SimHandle* h) {
   if (!h) return SIM_OK;
   cudaStreamSynchronize(h->stream);
+  for (auto& t : h->timed) { cudaEventDestroy(t.a); cudaEventDestroy(t.b); }
   if (h->graph) cudaGraphExecDestroy(h->graph);
   if (h->calib) calib_delete(h->calib);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);

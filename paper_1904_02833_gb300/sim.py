@@ -106,6 +106,18 @@ class SnakeSim:
         N.check(self.lib.sim_set_pressure(self.h, _ptr(u), 1))
         self._ucmd_keep = u
 
+    def kernel_timing(self, enable: bool = True):
+        """Record CUDA events around every solver kernel launch of sim_step / split calls."""
+        N.check(self.lib.sim_kernel_timing(self.h, 1 if enable else 0))
+
+    def kernel_times(self) -> dict:
+        """{(lanes, nodes per lane): (summed ms, launches)} since the last call."""
+        ms = np.zeros(12, np.float32)
+        n = np.zeros(12, np.int64)
+        N.check(self.lib.sim_kernel_times(self.h, ms.ctypes.data_as(ctypes.c_void_p),
+                                          n.ctypes.data_as(ctypes.c_void_p)))
+        return {(8 << (l // 4), l % 4 + 1): (float(ms[l]), int(n[l])) for l in range(12) if n[l]}
+
     def autotune(self, n_steps: int = 1):
         N.check(self.lib.sim_autotune(self.h, int(n_steps)))
 
