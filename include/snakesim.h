@@ -314,8 +314,12 @@ SimStatus sim_set_mlp(SimHandle* h, MlpHandle* m);
  * 6 * total_nodes (six slots per node). */
 SimStatus sim_split_begin(SimHandle* h);
 SimStatus sim_split_finish(SimHandle* h);
-/* Device pointer of the feature buffer [rows][32] bf16 and the row count. */
+/* Device pointer of the feature buffer [rows][32] bf16 and the row count.  The rows of
+ * one snake are consecutive (six per node, node by node) but the snakes are grouped by
+ * lane layout (so that the network runs once per layout on a contiguous range): snake s
+ * starts at row first_row[s] (sim_feature_offsets, host array of n_snakes). */
 SimStatus sim_features(SimHandle* h, void** feat, int64_t* rows);
+SimStatus sim_feature_offsets(SimHandle* h, int32_t* first_row);
 
 /* Text of the last error raised on the calling thread ("" if none). */
 const char* sim_last_error(void);

@@ -67,6 +67,7 @@ SIGNATURES = {
     "sim_set_layout": [H, ctypes.c_int, ctypes.c_int, ctypes.c_int],
     "sim_launch_count": [H, I64P],
     "sim_kernel_timing": [H, ctypes.c_int],
+    "sim_feature_offsets": [H, P],
     "sim_kernel_times": [H, P, P],
     "sim_destroy": [H],
     "sim_set_mlp": [H, H],

@@ -30,6 +30,7 @@ struct SolverArgs {
   int* status;            // [snakes]
   const int4* items;      // [n_items] (offset into order, snakes in item, layout id, 0)
   const int* order;       // snake indices grouped by layout
+  const int* feat_off;    // [snakes] first node of the snake in the feature / lam0 row order
   int n_items;
   int* work;              // work-queue counter of this launch (zeroed before the launch)
   const float* ucmd;      // [links] command override or null

@@ -218,6 +218,11 @@ struct SimHandle {
   int* order = nullptr;
   int n_items = 0;
   // device scheduling (schedule_kernel): class of each snake, class offsets, scratch
+  // feature rows: the snakes of one layout take consecutive rows (network per layout);
+  // snake s's rows start at 6 feat_off[s], layout l's nodes are [lay_fnode[l], lay_fnode[l+1])
+  int* feat_off_d = nullptr;
+  std::vector<int> feat_off;
+  long long lay_fnode[kLayouts + 1] = {};
   int4* items0 = nullptr;
   int *sched_cls = nullptr, *sched_base = nullptr, *sched_hist = nullptr, *sched_key = nullptr;
   int n_cls = 0;
@@ -357,6 +362,28 @@ SimStatus build_items(SimHandle* h, const std::map<int, int>* only_bucket = null
     CU(cudaMemcpy(h->sched_cls, cls.data(), h->n * sizeof(int), cudaMemcpyHostToDevice));
     CU(cudaMemcpy(h->sched_base, cls_base.data(), cls_base.size() * sizeof(int), cudaMemcpyHostToDevice));
   }
+  // feature offsets: layout by layout, snake by snake
+  h->feat_off.assign(h->n, 0);
+  {
+    long long cur = 0;
+    for (int l = 0; l < kLayouts; ++l) {
+      h->lay_fnode[l] = cur;
+      for (auto& kv : buckets) {
+        if (h->layout[kv.first] != l || (only_bucket && !only_bucket->count(kv.first))) continue;
+        for (int s : kv.second) { h->feat_off[s] = (int)cur; cur += kv.first; }
+      }
+    }
+    h->lay_fnode[kLayouts] = cur;
+    // snakes outside the scheduled classes keep their own rows past the end
+    for (auto& kv : buckets) {
+      if (!(only_bucket && !only_bucket->count(kv.first))) continue;
+      for (int s : kv.second) { h->feat_off[s] = (int)cur; cur += kv.first; }
+    }
+    if (h->feat_off_d) cudaFree(h->feat_off_d);
+    h->feat_off_d = nullptr;
+    CU(cudaMalloc(&h->feat_off_d, h->n * sizeof(int)));
+    CU(cudaMemcpy(h->feat_off_d, h->feat_off.data(), h->n * sizeof(int), cudaMemcpyHostToDevice));
+  }
   // per-layout ranges, grids, and launch order (most nodes x nodes per lane first)
   std::vector<double> work(kLayouts, 0.0);
   int cnt[kLayouts] = {};
@@ -390,6 +417,7 @@ SolverArgs make_args(SimHandle* h, int n_steps) {
   A.node_off = h->node_off_d; A.link_off = h->link_off_d;
   A.resid = h->resid; A.iters = h->iters; A.status = h->status;
   A.items = h->items; A.order = h->order; A.n_items = h->n_items;
+  A.feat_off = h->feat_off_d;
   A.work = h->work;
   A.ucmd = h->use_ucmd ? h->ucmd : nullptr;
   A.lam0 = (h->cfg.warm == SIM_WARM_LEARNED) ? h->lam0 : nullptr;
@@ -417,13 +445,29 @@ SolverArgs make_args(SimHandle* h, int n_steps) {
 }
 
 SimStatus launch_args(SimHandle* h, const SolverArgs& A, cudaStream_t st);
+SimStatus launch_layout(SimHandle* h, const SolverArgs& A, int l, cudaStream_t s);
+bool forked(const SimHandle* h);
+cudaStream_t lay_stream(SimHandle* h, int l, cudaStream_t st);
+SimStatus fork_layouts(SimHandle* h, cudaStream_t st);
+SimStatus join_layouts(SimHandle* h, cudaStream_t st);
+SimStatus launch_net(SimHandle* h, int l, cudaStream_t s);
 
-// Split mode: finish substep `sub` (if >= 0) and begin the next one.
-SimStatus launch_split(SimHandle* h, int sub, cudaStream_t st) {
+// Split mode: finish substep `sub` (if >= 0) and begin the next one; with `net`, each
+// layout's network launch precedes its solver kernel on the layout's stream.
+SimStatus launch_split(SimHandle* h, int sub, cudaStream_t st, bool net) {
+  if (h->n_items == 0) return SIM_OK;
   SolverArgs A = make_args(h, 0);
   A.split = 1;
   A.sub = sub;
-  return launch_args(h, A, st);
+  SimStatus r = fork_layouts(h, st);
+  for (int k = 0; k < h->n_lay && r == SIM_OK; ++k) {
+    const int l = h->lay_launch[k];
+    cudaStream_t s = lay_stream(h, l, st);
+    if (net) r = launch_net(h, l, s);
+    if (r == SIM_OK) r = launch_layout(h, A, l, s);
+  }
+  if (r == SIM_OK) r = join_layouts(h, st);
+  return r;
 }
 
 // Rebuilds the work queue from the last env-step's update counts.
@@ -447,17 +491,27 @@ SimStatus advance(SimHandle* h, int n, cudaStream_t st) {
   return SIM_OK;
 }
 
-// One env-step substep by substep, with the network between solver launches.
+// One env-step substep by substep, with the network between solver launches.  Each
+// layout's chain (solver kernel, network, solver kernel, ...) runs on its own stream
+// for the whole env-step: a substep of one layout waits only for its own snakes, and the
+// other layouts' work fills the tail of its launches.
 SimStatus split_step(SimHandle* h, cudaStream_t st) {
+  if (h->n_items == 0) return SIM_OK;
   SimStatus r = schedule(h, st);
-  if (r == SIM_OK) r = launch_split(h, -1, st);
-  for (int s = 0; s < h->cfg.n_sub && r == SIM_OK; ++s) {
-    if (h->cfg.warm == SIM_WARM_LEARNED) {
-      r = mlp_forward_launch(h->mlp, h->feat, h->n_nodes * 6, h->lam0, st);
-      h->launches += 1;
+  if (r == SIM_OK) r = fork_layouts(h, st);
+  const bool learned = h->cfg.warm == SIM_WARM_LEARNED;
+  for (int sub = -1; sub < h->cfg.n_sub && r == SIM_OK; ++sub) {
+    SolverArgs A = make_args(h, 0);
+    A.split = 1;
+    A.sub = sub;
+    for (int k = 0; k < h->n_lay && r == SIM_OK; ++k) {
+      const int l = h->lay_launch[k];
+      cudaStream_t s = lay_stream(h, l, st);
+      if (sub >= 0 && learned) r = launch_net(h, l, s);
+      if (r == SIM_OK) r = launch_layout(h, A, l, s);
     }
-    if (r == SIM_OK) r = launch_split(h, s, st);
   }
+  if (r == SIM_OK) r = join_layouts(h, st);
   if (r == SIM_OK) r = advance(h, 1, st);
   return r;
 }
@@ -478,45 +532,72 @@ SimStatus launch_steps(SimHandle* h, int n_steps, cudaStream_t st) {
   return r;
 }
 
-SimStatus launch_args(SimHandle* h, const SolverArgs& A, cudaStream_t st) {
-  if (h->n_items == 0) return SIM_OK;
-  // with kernel timing on, the layouts run one after another so that each event pair
-  // brackets one kernel alone
-  const bool fork = h->n_lay > 1 && !h->timing;
-  if (fork) CU(cudaEventRecord(h->ev_split, st));
+// One solver kernel over the items of layout l, on stream s.
+SimStatus launch_layout(SimHandle* h, const SolverArgs& A, int l, cudaStream_t s) {
+  SolverArgs B = A;
+  B.items = h->items + h->lay_first[l];
+  B.n_items = h->lay_first[l + 1] - h->lay_first[l];
+  B.work = h->work + l;
+  CU(cudaMemsetAsync(B.work, 0, sizeof(int), s));
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  CU(cudaStreamIsCapturing(s, &cap));
+  const bool timed = h->timing && cap == cudaStreamCaptureStatusNone;
+  SimHandle::Timed tm{l, nullptr, nullptr};
+  if (timed) {
+    CU(cudaEventCreate(&tm.a));
+    CU(cudaEventCreate(&tm.b));
+    CU(cudaEventRecord(tm.a, s));
+  }
+  const int var = solver_var(h);
+  kSolverKernels[A.split ? 1 : 0][var][l]<<<h->lay_grid[l], 128, var == kVarPcr ? pcr_smem_bytes(l) : 0, s>>>(B);
+  CU(cudaGetLastError());
+  if (timed) {
+    CU(cudaEventRecord(tm.b, s));
+    h->timed.push_back(tm);
+  }
+  h->launches += 1;
+  return SIM_OK;
+}
+
+// The layouts' streams: forked from st (or st itself when they run one after another:
+// a single layout, or kernel timing on, so that each event pair brackets one kernel).
+bool forked(const SimHandle* h) { return h->n_lay > 1 && !h->timing; }
+cudaStream_t lay_stream(SimHandle* h, int l, cudaStream_t st) { return forked(h) ? h->side[l] : st; }
+SimStatus fork_layouts(SimHandle* h, cudaStream_t st) {
+  if (!forked(h)) return SIM_OK;
+  CU(cudaEventRecord(h->ev_split, st));
+  for (int k = 0; k < h->n_lay; ++k) CU(cudaStreamWaitEvent(h->side[h->lay_launch[k]], h->ev_split, 0));
+  return SIM_OK;
+}
+SimStatus join_layouts(SimHandle* h, cudaStream_t st) {
+  if (!forked(h)) return SIM_OK;
   for (int k = 0; k < h->n_lay; ++k) {
     const int l = h->lay_launch[k];
-    SolverArgs B = A;
-    B.items = h->items + h->lay_first[l];
-    B.n_items = h->lay_first[l + 1] - h->lay_first[l];
-    B.work = h->work + l;
-    cudaStream_t s = fork ? h->side[l] : st;
-    if (fork) CU(cudaStreamWaitEvent(s, h->ev_split, 0));
-    CU(cudaMemsetAsync(B.work, 0, sizeof(int), s));
-    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
-    CU(cudaStreamIsCapturing(s, &cap));
-    const bool timed = h->timing && cap == cudaStreamCaptureStatusNone;
-    SimHandle::Timed tm{l, nullptr, nullptr};
-    if (timed) {
-      CU(cudaEventCreate(&tm.a));
-      CU(cudaEventCreate(&tm.b));
-      CU(cudaEventRecord(tm.a, s));
-    }
-    const int var = solver_var(h);
-    kSolverKernels[A.split ? 1 : 0][var][l]<<<h->lay_grid[l], 128, var == kVarPcr ? pcr_smem_bytes(l) : 0,
-                                              s>>>(B);
-    CU(cudaGetLastError());
-    if (timed) {
-      CU(cudaEventRecord(tm.b, s));
-      h->timed.push_back(tm);
-    }
-    h->launches += 1;
-    if (fork) {
-      CU(cudaEventRecord(h->ev_side[l], s));
-      CU(cudaStreamWaitEvent(st, h->ev_side[l], 0));
-    }
+    CU(cudaEventRecord(h->ev_side[l], h->side[l]));
+    CU(cudaStreamWaitEvent(st, h->ev_side[l], 0));
   }
   return SIM_OK;
+}
+
+// All layouts' kernels of one launch, overlapping on forked streams.
+SimStatus launch_args(SimHandle* h, const SolverArgs& A, cudaStream_t st) {
+  if (h->n_items == 0) return SIM_OK;
+  SimStatus r = fork_layouts(h, st);
+  for (int k = 0; k < h->n_lay && r == SIM_OK; ++k) {
+    const int l = h->lay_launch[k];
+    r = launch_layout(h, A, l, lay_stream(h, l, st));
+  }
+  if (r == SIM_OK) r = join_layouts(h, st);
+  return r;
+}
+
+// The network on the feature rows of layout l's snakes (contiguous, see feat_off).
+SimStatus launch_net(SimHandle* h, int l, cudaStream_t s) {
+  const long long r0 = 6LL * h->lay_fnode[l], r1 = 6LL * h->lay_fnode[l + 1];
+  if (r1 <= r0) return SIM_OK;
+  SimStatus r = mlp_forward_launch(h->mlp, h->feat + r0 * 32, r1 - r0, h->lam0 + r0, s);
+  h->launches += 1;
+  return r;
 }
 
 }  // namespace
@@ -901,7 +982,7 @@ SimStatus sim_split_begin(SimHandle* h) {
   if (!h) return fail(SIM_EINVAL, "null handle");
   if (h->cur_sub >= 0) return fail(SIM_EINVAL, "an env-step is already in progress");
   SimStatus st = schedule(h, h->stream);
-  if (st == SIM_OK) st = launch_split(h, -1, h->stream);
+  if (st == SIM_OK) st = launch_split(h, -1, h->stream, false);
   if (st != SIM_OK) return st;
   h->cur_sub = 0;
   return SIM_OK;
@@ -910,13 +991,9 @@ SimStatus sim_split_begin(SimHandle* h) {
 SimStatus sim_split_finish(SimHandle* h) {
   if (!h) return fail(SIM_EINVAL, "null handle");
   if (h->cur_sub < 0) return fail(SIM_EINVAL, "no env-step in progress (sim_split_begin)");
-  if (h->cfg.warm == SIM_WARM_LEARNED) {
-    if (!h->mlp) return fail(SIM_EINVAL, "learned warm start without a network (sim_set_mlp)");
-    SimStatus r = mlp_forward_launch(h->mlp, h->feat, h->n_nodes * 6, h->lam0, h->stream);
-    if (r != SIM_OK) return r;
-    h->launches += 1;
-  }
-  SimStatus st = launch_split(h, h->cur_sub, h->stream);
+  const bool learned = h->cfg.warm == SIM_WARM_LEARNED;
+  if (learned && !h->mlp) return fail(SIM_EINVAL, "learned warm start without a network (sim_set_mlp)");
+  SimStatus st = launch_split(h, h->cur_sub, h->stream, learned);
   if (st != SIM_OK) return st;
   h->cur_sub += 1;
   if (h->cur_sub >= h->cfg.n_sub) {
@@ -925,6 +1002,12 @@ SimStatus sim_split_finish(SimHandle* h) {
     h->cur_sub = -1;
     h->step_index += 1;
   }
+  return SIM_OK;
+}
+
+SimStatus sim_feature_offsets(SimHandle* h, int32_t* first_row) {
+  if (!h || !first_row) return fail(SIM_EINVAL, "null handle or output");
+  for (int s = 0; s < h->n; ++s) first_row[s] = 6 * h->feat_off[s];
   return SIM_OK;
 }
 
@@ -1049,7 +1132,7 @@ SimStatus sim_destroy(SimHandle* h) {
                   h->iters, h->status, h->items, h->order, h->ucmd, h->inv_mass_d, h->scratch3,
                   h->lam0, h->feat, h->snap_pos, h->snap_vel, h->snap_press, h->snap_lam,
                   h->step_dev, h->snap_step_dev, h->work, h->sched_cls, h->sched_base,
-                  h->sched_hist, h->sched_key, h->items0};
+                  h->sched_hist, h->sched_key, h->items0, h->feat_off_d};
   for (void* p : ptrs) if (p) cudaFree(p);
   delete h;
   return SIM_OK;

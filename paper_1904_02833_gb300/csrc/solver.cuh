@@ -106,7 +106,7 @@ __device__ __forceinline__ float group_max(float r) {
 
 // Per-group constants of one snake.
 struct SnakeK {
-  int N, seg, nfix, L, nb, lb;
+  int N, seg, nfix, L, nb, lb, fb;  // fb: first node of the snake in the feature row order
   float L0, inv_L0, inv_m, mass, at_s, at_b, mu, radius, gain, e_inf, e_def, damp_over_h;
   float mu_side, inv_mu, inv_mu_side;  // mu_side > 0: anisotropic friction (body frame)
 };
@@ -457,7 +457,7 @@ __device__ __forceinline__ void write_features(const SnakeK& S, const SolverArgs
         __nv_bfloat162 b2 = __floats2bfloat162_rn(f[2 * c], f[2 * c + 1]);
         pk[c] = *reinterpret_cast<uint32_t*>(&b2);
       }
-      uint4* dst = reinterpret_cast<uint4*>(A.feat + ((size_t)(S.nb + i) * 6 + k) * 32);
+      uint4* dst = reinterpret_cast<uint4*>(A.feat + ((size_t)(S.fb + i) * 6 + k) * 32);
 #pragma unroll
       for (int c = 0; c < 4; ++c) dst[c] = make_uint4(pk[4 * c], pk[4 * c + 1], pk[4 * c + 2], pk[4 * c + 3]);
     }
@@ -655,6 +655,7 @@ __device__ void run_group(const SolverArgs& A, int snake, bool valid, float* sme
   S.N = valid ? P.n_links * P.seg_per_link + 1 : 0;
   S.seg = P.seg_per_link; S.nfix = P.n_fixed; S.L = P.n_links;
   S.nb = valid ? A.node_off[snake] : 0;
+  S.fb = valid ? A.feat_off[snake] : 0;
   S.lb = valid ? A.link_off[snake] : 0;
   S.L0 = P.L0; S.inv_L0 = 1.0f / P.L0; S.inv_m = 1.0f / P.mass; S.mass = P.mass;
   S.at_s = P.alpha_s / (h * h); S.at_b = P.alpha_b / (h * h);
@@ -772,7 +773,7 @@ __device__ void run_group(const SolverArgs& A, int snake, bool valid, float* sme
 #pragma unroll
         for (int k = 0; k < 6; ++k) {
           float l = A.beta * lam[j][k];
-          if (A.warm == 2 && A.lam0 && valid && i < S.N) l += A.lam0[(size_t)(S.nb + i) * 6 + k] * sc;
+          if (A.warm == 2 && A.lam0 && valid && i < S.N) l += A.lam0[(size_t)(S.fb + i) * 6 + k] * sc;
           lam[j][k] = l;
         }
       }

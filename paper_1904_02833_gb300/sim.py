@@ -192,11 +192,20 @@ class SnakeSim:
     def split_finish(self):
         N.check(self.lib.sim_split_finish(self.h))
 
-    def features(self) -> torch.Tensor:
-        """The feature buffer [6 * nodes, 32] (bf16 view of library memory, zero copy)."""
+    def features(self, raw: bool = False) -> torch.Tensor:
+        """The features [6 * nodes, 32] bf16 in node order (row 6 i + k: node i, row kind k),
+        gathered from the library's buffer; raw=True: the buffer itself (zero copy, snakes
+        grouped by lane layout, see sim_feature_offsets)."""
         p, r = ctypes.c_void_p(), ctypes.c_int64()
         N.check(self.lib.sim_features(self.h, ctypes.byref(p), ctypes.byref(r)))
-        return _view_bf16(p.value, r.value * 32, self.device).view(r.value, 32)
+        buf = _view_bf16(p.value, r.value * 32, self.device).view(r.value, 32)
+        if raw:
+            return buf
+        first = np.zeros(self.n, np.int32)
+        N.check(self.lib.sim_feature_offsets(self.h, first.ctypes.data_as(ctypes.c_void_p)))
+        rows = np.diff(self.node_off) * 6
+        idx = np.repeat(first.astype(np.int64) - 6 * self.node_off[:-1], rows) + np.arange(6 * self.n_nodes)
+        return buf[torch.as_tensor(idx, device=self.device)]
 
     def status(self):
         st = np.zeros(self.n, np.int32)
