@@ -103,6 +103,37 @@ def test_every_layout_matches_oracle():
             g.close()
 
 
+def test_extreme_sizes_match_oracle():
+    """The longest snake the lane layouts hold (128 nodes: 32 lanes x 4 nodes) beside the
+    shortest (2 nodes, one stretch row), with a learned-mode-sized grid of tiny and huge
+    snakes mixed, against the oracle; the 128-node snake at its one admissible layout."""
+    w = W.batched(n=12, seed=41, links=(1, 8))
+    w["n_links"][:] = [1, 1, 12, 3, 1, 12, 5, 1, 8, 2, 1, 7]
+    w["seg_per_link"][:] = [1, 10, 10, 10, 127, 10, 10, 1, 10, 10, 2, 10]
+    nodes = W.n_nodes(w)
+    assert nodes.max() == 128 and nodes.min() == 2
+    s = W.solver_settings(iters=10)
+    g, o = Sim(w, s), oracle.OracleSim(w, s)
+    assert g.layout(128) == (32, 4)
+    for _ in range(2):
+        g.step(1)
+        o.step(1)
+        compare(g, o)
+
+
+def test_mixed_isotropic_and_anisotropic_batch():
+    """Half the snakes with anisotropic friction, half isotropic, in one batch: the
+    kernels with the anisotropic path compiled in run both kinds."""
+    w = W.batched(n=40, seed=42, links=(1, 8))
+    w["mu_side"] = np.where(np.arange(40) % 2 == 0, 3.0 * w["mu"], 0.0)
+    s = W.solver_settings(iters=10)
+    g, o = Sim(w, s), oracle.OracleSim(w, s)
+    for _ in range(3):
+        g.step(2)
+        o.step(2)
+        compare(g, o)
+
+
 def test_trajectory_before_contact():
     """One second (60 env-steps) of a gait-driven snake in the air: 1e-3 m."""
     w = W.subset(W.batched(n=8, seed=5), range(8))
