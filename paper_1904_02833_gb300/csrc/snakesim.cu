@@ -3,8 +3,11 @@
 // Owns the structure-of-arrays state in HBM (float4 positions with inverse mass,
 // float4 velocities, float2 chamber pressures, six multipliers per node), buckets the
 // snakes by node count, picks a lane layout per bucket (lanes per snake x nodes per
-// lane, optionally by timing them: sim_autotune) and launches the persistent solver
-// kernel, directly or through a captured CUDA graph.
+// lane, optionally by timing them: sim_autotune), rebuilds the work queues on the device
+// before every env-step (schedule_kernel) and launches one persistent solver kernel per
+// layout (Jacobi, Jacobi with anisotropic friction, or Newton + PCR), directly or through
+// a captured CUDA graph; in the learned mode each layout runs its own chain of solver and
+// network launches, substep by substep, on its own stream.
 #include <cuda_runtime.h>
 
 #include <algorithm>
