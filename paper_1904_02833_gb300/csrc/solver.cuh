@@ -18,11 +18,14 @@
 //
 // The arithmetic of every step cites the paper (Gasoto et al., arXiv 1904.02833):
 //   gait              Eq. 9 (Sec. V-A)
-//   chambers          antagonistic pair, Sec. III; first-order latency (Sec. V-A's
-//                     latency model replaced by exact exponential relaxation)
+//   chambers          antagonistic pair, Sec. III; first-order latency (exact
+//                     exponential relaxation) or the discrete law of Sec. V-A (Eq. 11-12)
 //   rest angle        Eq. 3-4 with the inextensible centre layer of Sec. V
-//   rows              c + E lambda = 0 (Sec. IV), contact Eq. 7, Coulomb cone (Sec. IV)
-//   Jacobi relaxation Eq. 8 with its diagonal (Sec. IV-D)
+//   rows              c + E lambda = 0 (Sec. IV), contact Eq. 7, Coulomb cone (Sec. IV),
+//                     optionally anisotropic in the body frame (the wheels of Sec. V)
+//   Jacobi relaxation Eq. 8 with its diagonal (Sec. IV-D); or Newton steps with a
+//                     preconditioned conjugate residual solve of Eq. 8 (Sec. IV-D,
+//                     contact-free substeps; pcr.cuh)
 #pragma once
 
 #include <cuda_runtime.h>
