@@ -327,13 +327,9 @@ def run_gpu(args):
             "plain_value": modes_out["plain"]["value"],
             "learned_vs_plain": value / modes_out["plain"]["value"],
             "modes": modes_out,
-            "config": {"workload": "%d uneven snakes (2-8 links x 10 segments, %d nodes), dt 1/60 s,"
-                                   " 20 substeps, Jacobi to residual %g (cap %d updates/substep)"
-                                   % (N_SNAKES, total_nodes, TOL, CAP),
-                       "snakes_per_gpu": N_SNAKES, "nodes_per_gpu": total_nodes,
-                       "l2": "flushed between timed steps (256 MB write)",
-                       "parallelism": "independent snakes per GPU (dp%d)" % world,
-                       "training": {"seconds": round(t_train, 1), "rounds": record}},
+            "config": dict(workload_config(total_nodes, world),
+                           l2="flushed between timed steps (256 MB write)",
+                           training={"seconds": round(t_train, 1), "rounds": record}),
             "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
                          "frac": achieved / alu_peak, "traffic": traffic,
                          "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one "
@@ -480,6 +476,15 @@ def cpu_baseline(w, s, n_sample=None, budget_s=20.0):
                       "%.1f s" % (n_sample, steps, dt)}
 
 
+def workload_config(total_nodes, world):
+    """The benchmark's workload, the same in both arms."""
+    return {"workload": "%d uneven snakes (2-8 links x 10 segments, %d nodes), dt 1/60 s,"
+                        " 20 substeps, Jacobi to residual %g (cap %d updates/substep)"
+                        % (N_SNAKES, total_nodes, TOL, CAP),
+            "snakes_per_gpu": N_SNAKES, "nodes_per_gpu": total_nodes,
+            "parallelism": "independent snakes per GPU (dp%d)" % world}
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -506,8 +511,7 @@ def run_reference(args):
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "%d uneven snakes (2-8 links x 10 segments), dt 1/60 s, 20 substeps,"
-                               " Jacobi to residual %g" % (N_SNAKES, TOL)},
+        "config": workload_config(int(W.n_nodes(w).sum()), world),
         "cpu_baseline": {"value": value, "unit": "env-steps/s", "cores": cores, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": "env-steps/s", "h2d_bytes_per_step": 0,
