@@ -4,7 +4,8 @@ Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.
 this package.  It is independent of the CUDA path: it shares no kernels, headers or
 helpers with it and never imports it.  The arithmetic lives in ``snake_oracle.cpp`` (plain
 loops, FP64, templated on a dual-number type for parameter derivatives) and
-``mlp_oracle.py`` (the warm-start network in FP64).
+``mlp_oracle.py`` (the warm-start network in FP64); the tetrahedral soft link in
+``fem_oracle.cpp`` (wrapped by ``fem.py``).
 
 Parity unpinned: the full locomotion runs (one 4-link snake, batched snakes) have no
 closed form and no published trajectory data; they are checked only against this
@@ -20,7 +21,7 @@ import subprocess
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "snake_oracle.cpp")
+_SRCS = [os.path.join(_HERE, f) for f in ("snake_oracle.cpp", "fem_oracle.cpp")]
 _LIB = os.path.join(_HERE, "liboracle.so")
 
 PRM_FIELDS = ("L0", "mass", "alpha_s", "alpha_b", "gain", "tau_inf", "tau_def", "mu",
@@ -32,9 +33,9 @@ _lib = None
 
 def build(force: bool = False) -> str:
     """Compile the oracle shared library with the host compiler."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(map(os.path.getmtime, _SRCS)):
         tmp = _LIB + ".tmp%d" % os.getpid()
-        cmd = ["g++", "-O2", "-std=c++17", "-fopenmp", "-fPIC", "-shared", _SRC, "-o", tmp]
+        cmd = ["g++", "-O2", "-std=c++17", "-fopenmp", "-fPIC", "-shared"] + _SRCS + ["-o", tmp]
         subprocess.run(cmd, check=True)
         os.replace(tmp, _LIB)
     return _LIB
@@ -55,6 +56,10 @@ def lib():
         L.oracle_features.argtypes = [ctypes.c_int, P, P, P, P, P, ctypes.c_longlong, P, P, P, P,
                                       P, P]
         L.oracle_mlp_forward.argtypes = [P, ctypes.c_longlong, P, P]
+        L.fem_oracle_polar.argtypes = [P, P, P]
+        L.fem_oracle_tet.argtypes = [P, P, P, P, P, P]
+        L.fem_oracle_step.argtypes = [ctypes.c_int] * 4 + [P] * 7 + [ctypes.c_longlong, ctypes.c_int,
+                                                                     P, P, P, P, ctypes.c_int, ctypes.c_int]
         assert L.oracle_nprm() == len(PRM_FIELDS)
         _lib = L
     return _lib

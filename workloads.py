@@ -178,3 +178,116 @@ def pendulum(length: float = 0.1) -> dict:
     w["damping"][:] = 0.0
     w["gait_amp"][:] = 0.0
     return w
+
+
+# ---------------------------------------------------------------- tetrahedral soft link
+# A soft link as the paper models it (Sec. III-A, III-B, IV): a solid silicone body meshed
+# with tetrahedra, an inextensible layer along its centre plane, a perimeter held by the
+# fibre reinforcement and actuation distance rows along the chambers.  The paper meshes
+# its link with TetGen; this generator stands in for that mesh with a radially symmetric
+# one of the same kind: `n_sec` cross-sections along the axis (the paper uses 13), each a
+# centre particle and two rings of `m` particles (radius R/2 and R), every cross-section
+# triangle swept to the next section as a prism split into three tetrahedra.  Geometry and
+# connectivity only; no mechanics.
+
+FEM_FLOAT_FIELDS = ("youngs", "poisson", "density", "damping", "alpha_inext", "alpha_perim",
+                    "alpha_act", "press_amp", "press_freq", "press_phase", "press_offset")
+
+# Ecoflex 00-30 (Sec. V: Y = 66.243 kPa, nu = 0.4999; specific gravity 1.07), hard
+# inextensible and perimeter rows, compliant actuation rows, a 2 psi, 1 Hz pressure wave.
+FEM_DEFAULTS = dict(youngs=66243.0, poisson=0.4999, density=1070.0, damping=1.0,
+                    alpha_inext=0.0, alpha_perim=0.0, alpha_act=1e-3, press_amp=13790.0,
+                    press_freq=1.0, press_phase=0.0, press_offset=0.0)
+
+# distance-row kinds of the link mesh
+FEM_INEXT, FEM_PERIM, FEM_ACT_LEFT, FEM_ACT_RIGHT = 0, 1, 2, 3
+
+
+def fem_link_mesh(m: int = 8, n_sec: int = 13, length: float = 0.1, radius: float = 0.0125) -> dict:
+    """Rest particles [P, 3] (axis along x, cross-section point (y, z) = rho (cos phi, sin phi)
+    with phi = 2 pi k / m), positively oriented tetrahedra [T, 4], distance rows [D, 2] with
+    their kinds [D] and the fixed flags [P] (the first cross-section, held by its rigid
+    cap).  The centre plane y = 0 carries the inextensible layer; the left chamber is y > 0,
+    the right one y < 0.  m must be a multiple of 4 (particles on the centre plane)."""
+    assert m % 4 == 0 and m >= 4 and n_sec >= 2
+    per = 1 + 2 * m
+
+    def pid(s, ring, k):
+        return s * per + (0 if ring == 0 else 1 + (ring - 1) * m + (k % m))
+
+    phi = 2.0 * math.pi * np.arange(m) / m
+    cphi = np.round(np.cos(phi), 12)
+    X = np.zeros((n_sec * per, 3))
+    for s in range(n_sec):
+        xs = length * s / (n_sec - 1)
+        X[pid(s, 0, 0)] = (xs, 0.0, 0.0)
+        for ring, rho in ((1, 0.5 * radius), (2, radius)):
+            for k in range(m):
+                X[pid(s, ring, k)] = (xs, rho * math.cos(phi[k]), rho * math.sin(phi[k]))
+    tris = []
+    for k in range(m):
+        tris.append((pid(0, 0, 0), pid(0, 1, k), pid(0, 1, k + 1)))
+        tris.append((pid(0, 1, k), pid(0, 2, k), pid(0, 2, k + 1)))
+        tris.append((pid(0, 1, k), pid(0, 2, k + 1), pid(0, 1, k + 1)))
+    tets = []
+    for s in range(n_sec - 1):
+        for tri in tris:
+            a, b, c = sorted(v + s * per for v in tri)
+            A, B, C = a + per, b + per, c + per
+            # sorted-vertex split: the diagonal of every side face depends only on the
+            # order of its two bottom vertices, so neighbouring prisms agree
+            for t in ((a, b, c, A), (b, c, A, B), (c, A, B, C)):
+                e1, e2, e3 = X[t[1]] - X[t[0]], X[t[2]] - X[t[0]], X[t[3]] - X[t[0]]
+                tets.append(t if np.dot(np.cross(e1, e2), e3) > 0 else (t[0], t[2], t[1], t[3]))
+    rows, kinds = [], []
+    for s in range(n_sec - 1):
+        plane = [pid(s, 0, 0)] + [pid(s, r, k) for r in (1, 2) for k in range(m) if cphi[k] == 0.0]
+        for p in plane:
+            rows.append((p, p + per)); kinds.append(FEM_INEXT)
+    for s in range(n_sec):
+        for k in range(m):
+            rows.append((pid(s, 2, k), pid(s, 2, k + 1))); kinds.append(FEM_PERIM)
+    for s in range(n_sec - 1):
+        for side, kind in ((1.0, FEM_ACT_LEFT), (-1.0, FEM_ACT_RIGHT)):
+            for r in (1, 2):
+                for k in range(m):
+                    if cphi[k] * side > 0.0:
+                        rows.append((pid(s, r, k), pid(s + 1, r, k))); kinds.append(kind)
+    fixed = np.zeros(n_sec * per, np.int32)
+    fixed[:per] = 1
+    return dict(X=X, tets=np.asarray(tets, np.int32), rows=np.asarray(rows, np.int32),
+                kinds=np.asarray(kinds, np.int32), fixed=fixed)
+
+
+def fem_settings(dt=1.0 / 60.0, n_sub=2, iters=21, tol=0.0, pcr_iters=20, gravity=(0.0, 0.0, 0.0)):
+    """Global settings of the link solve: frame dt, substeps (the paper's benchmark runs 2
+    per frame with 20 solver iterations each), the cap on matrix-vector products per
+    substep, the residual tolerance that ends the Newton loop (0 = run to the cap), PCR
+    iterations per Newton step and gravity (off: the link rests on its wheels)."""
+    return dict(dt=float(dt), n_sub=int(n_sub), iters=int(iters), tol=float(tol),
+                pcr_iters=int(pcr_iters), gravity=tuple(float(g) for g in gravity))
+
+
+def fem_links(n: int = 1216, seed: int = 6) -> dict:
+    """Batch of soft links on the same mesh: Young's modulus U[0.8, 1.2] x 66.243 kPa,
+    the paper's Poisson ratio, pressure amplitude U[1, 3] psi, frequency U[0.5, 2] Hz,
+    phase U[0, 2 pi)."""
+    rng = np.random.default_rng(seed)
+    w = {k: np.full(n, FEM_DEFAULTS[k], dtype=np.float64) for k in FEM_FLOAT_FIELDS}
+    w["youngs"][:] = FEM_DEFAULTS["youngs"] * rng.uniform(0.8, 1.2, size=n)
+    w["press_amp"][:] = 6894.76 * rng.uniform(1.0, 3.0, size=n)
+    w["press_freq"][:] = rng.uniform(0.5, 2.0, size=n)
+    w["press_phase"][:] = rng.uniform(0.0, 2 * math.pi, size=n)
+    return w
+
+
+def fem_const_pressure(n: int, press, **kw) -> dict:
+    """Links held at constant pressures `press` (Pa, signed: > 0 inflates the right
+    chamber, < 0 the left one)."""
+    w = {k: np.full(n, FEM_DEFAULTS[k], dtype=np.float64) for k in FEM_FLOAT_FIELDS}
+    w["press_amp"][:] = np.abs(np.broadcast_to(np.asarray(press, np.float64), (n,)))
+    w["press_freq"][:] = 0.0
+    w["press_phase"][:] = np.where(np.broadcast_to(np.asarray(press), (n,)) < 0, -math.pi / 2, math.pi / 2)
+    for k, v in kw.items():
+        w[k][:] = v
+    return w
