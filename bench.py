@@ -277,6 +277,7 @@ def run_gpu(args):
 
     solvers = None if args.no_solver_comparison else solver_comparison(args, flush, stream, local)
     calib = None if args.no_calibration else calibration_leg(stream)
+    fem = None if args.no_fem else fem_link_leg(flush, stream)
 
     if rank == 0:
         pk = peaks()
@@ -361,6 +362,8 @@ def run_gpu(args):
             res["solver_comparison"] = solvers
         if calib is not None:
             res["calibration"] = calib
+        if fem is not None:
+            res["fem_link"] = fem
         if world == 1 and not args.no_cpu_baseline:
             res["cpu_baseline"] = cpu_baseline(w, W.solver_settings(iters=CAP, tol=TOL, warm=W_COLD))
         print(json.dumps(res), flush=True)
@@ -410,6 +413,67 @@ def solver_comparison(args, flush, stream, local, n=4096, steps=3):
         out[name] = {"ms_per_step": float(np.mean(ms)), "env_steps_per_s": n * steps / (sum(ms) / 1e3),
                      "updates_per_substep": round(float(np.mean(upd)), 2), "residual_max": rmax}
     sim.close()
+    return out
+
+
+# Arithmetic of the soft-link kernel per element, counted from its code (rounded): one
+# product with its PCR vector updates (scatter 120, particle sums 14, element rows 145,
+# vector updates and dot products 84) and one linearisation (deformation gradient, polar
+# iteration, strains, diagonal and right-hand side 500) plus the final M^-1 J^T dlambda
+# (130); per substep at one Newton step: 363 x products + 2 x 500 + 130.
+FEM_FLOP_PER_ELEMENT_PRODUCT = 363
+FEM_FLOP_PER_ELEMENT_SUBSTEP = 2 * 500 + 130
+
+
+def fem_link_leg(flush, stream, n=1216, frames=10, warmup=3):
+    """The tetrahedral soft link (Sec. III-B; the paper's frame: 2 substeps, 20 PCR
+    iterations each): a batch of 1216 links (8 per SM) on the 13-cross-section mesh, one
+    thread block per link, timed per frame with CUDA events, L2 flushed between frames;
+    the FP64 oracle on the host cores on a sample of the batch for comparison."""
+    import torch
+    from paper_1904_02833_gb300.fem import FemSim
+    import oracle.fem as OF
+    M = W.fem_link_mesh()
+    w = W.fem_links(n, seed=6)
+    s = W.fem_settings()
+    sim = FemSim(M, w, s)
+    sim.step(warmup)
+    ms = []
+    for _ in range(frames):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        sim.step(1)
+        b.record(stream)
+        b.synchronize()
+        ms.append(a.elapsed_time(b))
+    x, v, r, mv = sim.state()
+    t = float(np.mean(ms))
+    NT = len(M["tets"])
+    flop = NT * (FEM_FLOP_PER_ELEMENT_PRODUCT * float(mv.astype(np.float64).sum())
+                 + FEM_FLOP_PER_ELEMENT_SUBSTEP * s["n_sub"] * n)
+    alu_peak = 152 * 128 * 2 * 2070.0 * 1e6 / 1e12
+    achieved = flop / (t / 1e3) / 1e12
+    cores = os.cpu_count() or 1
+    sample = W.fem_links(n, seed=6)
+    sel = np.arange(cores)
+    o = OF.OracleFem(M, {k: a[sel] for k, a in sample.items()}, s, n_threads=cores)
+    t0 = time.perf_counter()
+    o.step(2)
+    dt_o = time.perf_counter() - t0
+    out = {"workload": "%d soft links x %d elements, %d particles, %d distance rows; frame 1/60 s = %d substeps"
+                       " x (1 Newton step, %d PCR iterations)" % (n, NT, len(M["X"]), len(M["rows"]),
+                                                                  s["n_sub"], s["pcr_iters"]),
+           "ms_per_frame": t, "link_frames_per_s": n / (t / 1e3),
+           "products_per_substep": float(mv.mean()) / s["n_sub"],
+           "residual_mean": float(r.mean()), "residual_max": float(r.max()),
+           "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+                        "frac": achieved / alu_peak, "traffic": None,
+                        "flop_model": "elements x (363 per product + 1130 per substep)"},
+           "cpu_oracle": {"link_frames_per_s": len(sel) * 2 / dt_o, "cores": cores,
+                          "sample": "%d links x 2 frames (FP64, OpenMP over links)" % len(sel)},
+           "paper_context": "Table II: one FEM link 5.70 ms per frame on a GTX 1080 Ti"}
+    del sim
     return out
 
 
@@ -531,6 +595,8 @@ def main():
                     help="skip the Jacobi vs Newton + PCR leg (contact-free batch)")
     ap.add_argument("--no-calibration", action="store_true",
                     help="skip the differentiable calibration leg (forward + adjoint)")
+    ap.add_argument("--no-fem", action="store_true",
+                    help="skip the tetrahedral soft-link leg")
     ap.add_argument("--save-net", default=None, help="write the trained network parameters (.npy)")
     ap.add_argument("--load-net", default=None, help="use saved network parameters instead of training")
     ap.add_argument("--snakes", type=int, default=N_SNAKES,

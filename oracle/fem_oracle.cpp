@@ -481,7 +481,8 @@ void fem_step_t(int n_links, const Mesh& M, const double* prm, const double* cfg
     double r = 0.0;
     int mv_tot = 0;
     for (int f = 0; f < n_frames; ++f) {
-      r = 0.0;  // reported: the largest residual over the last frame's substeps
+      r = 0.0;  // reported: the largest residual and the products of the last frame
+      mv_tot = 0;
       for (int s = 0; s < n_sub; ++s) {
         int mvs = 0;
         const double t_s = (double)((frame + f) * n_sub + s) * h;
@@ -538,7 +539,7 @@ void fem_oracle_tet(const double* Xr, const double* x, double* c, double* G, dou
 
 // Advance n_links links (one shared mesh) by n_frames frames from frame index `frame`.
 // X, V: [n_links][P][3] in and out; resid: max residual of the last frame's substeps;
-// mv: matrix-vector products over the call.  fp32 != 0 runs the same steps in float
+// mv: matrix-vector products of the last frame.  fp32 != 0 runs the same steps in float
 // arithmetic (used only to size parity tolerances).
 void fem_oracle_step(int n_links, int P, int NT, int ND, const double* Xrest, const int* tets,
                      const int* rows, const int* kinds, const int* fixed, const double* prm,

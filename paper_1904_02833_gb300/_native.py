@@ -1,4 +1,5 @@
-"""ctypes binding of libsnakesim.so (the C-ABI declared in include/snakesim.h).
+"""ctypes binding of libsnakesim.so (the C-ABI declared in include/snakesim.h and
+include/femlink.h).
 
 Argument marshalling only: every step of the simulation runs in the library's CUDA
 kernels.  Loading fails loudly when the library has not been built; there is no
@@ -40,6 +41,26 @@ class SnakeParams(ctypes.Structure):
 
 assert ctypes.sizeof(SnakeParams) == 96
 assert ctypes.sizeof(SimConfig) == 80
+
+
+# tetrahedral soft link (include/femlink.h)
+class FemConfig(ctypes.Structure):
+    _fields_ = [("dt", ctypes.c_double), ("n_sub", ctypes.c_int32), ("iters", ctypes.c_int32),
+                ("tol", ctypes.c_float), ("pcr_iters", ctypes.c_int32), ("gravity", ctypes.c_float * 3)]
+
+
+FEM_FLOAT_FIELDS = ("youngs", "poisson", "density", "damping", "alpha_inext", "alpha_perim", "alpha_act",
+                    "press_amp", "press_freq", "press_phase", "press_offset")
+
+
+class FemLinkParams(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_float) for f in FEM_FLOAT_FIELDS]
+
+
+class FemMesh(ctypes.Structure):
+    _fields_ = [("n_particles", ctypes.c_int32), ("n_tets", ctypes.c_int32), ("n_rows", ctypes.c_int32),
+                ("rest", ctypes.c_void_p), ("tets", ctypes.c_void_p), ("rows", ctypes.c_void_p),
+                ("kinds", ctypes.c_void_p), ("fixed", ctypes.c_void_p)]
 
 _lib = None
 P = ctypes.c_void_p
@@ -87,6 +108,15 @@ SIGNATURES = {
     "mlp_check": [H],
     "mlp_destroy": [H],
     "mlp_forward_noalloc": [P, ctypes.c_int32, P, ctypes.c_int64, P, P],
+    "fem_create": [ctypes.POINTER(FemConfig), ctypes.POINTER(FemMesh), ctypes.c_int,
+                   ctypes.POINTER(FemLinkParams), P, ctypes.POINTER(H)],
+    "fem_set_config": [H, ctypes.POINTER(FemConfig)],
+    "fem_step": [H, ctypes.c_int],
+    "fem_get_state": [H, P, P, P, P, ctypes.c_int],
+    "fem_set_state": [H, P, P, ctypes.c_int],
+    "fem_set_frame": [H, ctypes.c_int64],
+    "fem_launch_count": [H, I64P],
+    "fem_destroy": [H],
 }
 MLP_NUM_PARAMS = 19841
 
