@@ -120,28 +120,33 @@ struct FemArgs {
 
 __device__ __forceinline__ float fin_or_inf(float a) { return (a <= 3.0e38f) ? a : INFINITY; }
 
-// Sum over the block, every thread gets the same value (partials added in warp order).
-__device__ __forceinline__ float block_sum(float a, float* red) {
+// Sum / maximum over the block; every thread gets the same value (partials combined in
+// warp order).  Consecutive reductions alternate between two halves of `red`, so one
+// barrier per reduction suffices: a half is rewritten two reductions later, after every
+// thread has passed the barrier of the reduction in between.
+__device__ __forceinline__ float block_sum(float a, float* red, int& k) {
 #pragma unroll
   for (int o = 16; o >= 1; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
   const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  if ((threadIdx.x & 31) == 0) red[w] = a;
+  float* r = red + 32 * (k & 1);
+  ++k;
+  if ((threadIdx.x & 31) == 0) r[w] = a;
   __syncthreads();
   float s = 0.f;
-  for (int i = 0; i < nw; ++i) s += red[i];
-  __syncthreads();
+  for (int i = 0; i < nw; ++i) s += r[i];
   return s;
 }
 
-__device__ __forceinline__ float block_max(float a, float* red) {
+__device__ __forceinline__ float block_max(float a, float* red, int& k) {
 #pragma unroll
   for (int o = 16; o >= 1; o >>= 1) a = fmaxf(a, __shfl_xor_sync(0xffffffffu, a, o));
   const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  if ((threadIdx.x & 31) == 0) red[w] = a;
+  float* r = red + 32 * (k & 1);
+  ++k;
+  if ((threadIdx.x & 31) == 0) r[w] = a;
   __syncthreads();
   float s = 0.f;
-  for (int i = 0; i < nw; ++i) s = fmaxf(s, red[i]);
-  __syncthreads();
+  for (int i = 0; i < nw; ++i) s = fmaxf(s, r[i]);
   return s;
 }
 
@@ -275,6 +280,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) fem_frame_kernel(FemArgs A) {
   const float damp = expf(-pr.damping * h);
   float r_frame = 0.f;
   int mv_frame = 0;
+  int nred = 0;  // reductions so far (selects the half of `red`)
 
   float R[kTPT][9], z[kTPT][6], p[kTPT][6], q[kTPT][6], dl[kTPT][6], az[kTPT][6];
 
@@ -457,7 +463,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) fem_frame_kernel(FemArgs A) {
         dp[d] = zd;
         ddl[d] = 0.f;
       }
-      const float r_all = block_max(rloc, red);  // (its barrier also publishes dn, dz, did)
+      const float r_all = block_max(rloc, red, nred);  // (its barrier also publishes dn, dz, did)
       r_sub = r_all;
       if (r_all <= A.tol || mv >= A.K) break;
       // ---- PCR from dlambda = 0 with the diagonal preconditioner
@@ -471,7 +477,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) fem_frame_kernel(FemArgs A) {
 #pragma unroll
           for (int k = 0; k < 6; ++k) { q[s][k] = az[s][k]; part += z[s][k] * az[s][k]; }
       for (int d = tid; d < ND; d += nthr) { dq[d] = daz[d]; part += dz[d] * daz[d]; }
-      float zaz = block_sum(part, red);
+      float zaz = block_sum(part, red, nred);
       for (int it = 0; it < A.pcr_iters && mv < A.K; ++it) {
         float qs = 0.f;
 #pragma unroll
@@ -482,7 +488,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) fem_frame_kernel(FemArgs A) {
             for (int k = 0; k < 6; ++k) qs += q[s][k] * q[s][k] * idT[6 * t + k];
         }
         for (int d = tid; d < ND; d += nthr) qs += dq[d] * dq[d] * did[d];
-        qs = block_sum(qs, red);
+        qs = block_sum(qs, red, nred);
         if (!(qs > 0.f)) break;
         const float alpha = zaz / qs;
 #pragma unroll
@@ -499,7 +505,8 @@ __global__ void __launch_bounds__(kMaxThreads, 1) fem_frame_kernel(FemArgs A) {
           ddl[d] += alpha * dp[d];
           dz[d] -= alpha * dq[d] * did[d];
         }
-        __syncthreads();  // dz complete before phase A reads it
+        // (phase A reads only this thread's rows; the particle sums it is about to
+        // overwrite were last read before the barrier of the reduction above)
         product(false);
         rows_of_u();
         ++mv;
@@ -510,7 +517,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) fem_frame_kernel(FemArgs A) {
 #pragma unroll
             for (int k = 0; k < 6; ++k) part += z[s][k] * az[s][k];
         for (int d = tid; d < ND; d += nthr) part += dz[d] * daz[d];
-        const float zaz_new = block_sum(part, red);
+        const float zaz_new = block_sum(part, red, nred);
         const float beta = zaz_new / zaz;
         zaz = zaz_new;
 #pragma unroll
@@ -535,8 +542,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) fem_frame_kernel(FemArgs A) {
           for (int k = 0; k < 6; ++k) lamT[6 * t + k] += dl[s][k];
       }
       for (int d = tid; d < ND; d += nthr) dlam[d] += ddl[d];
-      __syncthreads();  // ddl complete before phase A reads it
-      product(true);
+      product(true);  // (as above: the last reduction's barrier separates the reads of uu)
       for (int i = tid; i < P * 3; i += nthr) xx[i] += uu[i];
       __syncthreads();
     }

@@ -108,3 +108,39 @@ class FemSim:
         vs = None if v is None else np.ascontiguousarray(v, np.float32)
         p = lambda a: None if a is None else a.ctypes.data_as(ctypes.c_void_p)
         N.check(self.lib.fem_set_state(self.h, p(xs), p(vs), 0))
+
+
+def _main():
+    """Times a batch of soft links on the synthetic 13-cross-section mesh (one launch per
+    frame, CUDA events on the stream):  python -m paper_1904_02833_gb300.fem --links N
+    --frames F."""
+    import argparse
+    import json
+    import os
+    import sys
+
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import workloads as W
+
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--links", type=int, default=1216)
+    ap.add_argument("--frames", type=int, default=3)
+    a = ap.parse_args()
+    M = W.fem_link_mesh()
+    sim = FemSim(M, W.fem_links(a.links, seed=6), W.fem_settings())
+    st = torch.cuda.current_stream()
+    ms = []
+    for _ in range(a.frames):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        sim.step(1)
+        e1.record(st)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    x, v, r, mv = sim.state()
+    print(json.dumps({"links": a.links, "frames": a.frames, "ms_per_frame": ms, "residual_max": float(r.max()),
+                      "products_last_frame": int(mv.max()), "finite": bool(np.isfinite(x).all())}))
+
+
+if __name__ == "__main__":
+    _main()
