@@ -48,7 +48,8 @@ SimStatus ffail(SimStatus s, const std::string& msg) {
 
 // Offsets (in elements of each type) of the shared-memory areas of one block.
 struct FemLayout {
-  // floats
+  // floats (per-element arrays component-major: [component][element], so consecutive
+  // threads touch consecutive words)
   int g, vol, lam, idg, cont, xs, xx, vv, uu, wn, dn, drest, dat, did, dlam, ddl, dz, dp, dq, daz, red, n_float;
   // unsigned shorts (after the floats)
   int tet, row, coff, csr, n_short;
@@ -61,7 +62,7 @@ struct FemLayout {
     vol = o; o += NT;
     lam = o; o += NT * 6;
     idg = o; o += NT * 6;
-    cont = o; o += (4 * NT + 2 * ND) * 3;
+    cont = o; o += 18 * (NT > ND ? NT : ND);  // [18][S]: element vertex a comp k at 3a + k, row end e at 12 + 3e + k
     xs = o; o += P * 3;
     xx = o; o += P * 3;
     vv = o; o += P * 3;
@@ -78,6 +79,7 @@ struct FemLayout {
     dq = o; o += ND;
     daz = o; o += ND;
     red = o; o += 64;
+    o = (o + 3) & ~3;  // the vertex ids that follow are read as 8-byte words
     n_float = o;
     int s = 0;
     tet = s; s += NT * 4;
@@ -104,13 +106,13 @@ struct FemArgs {
   const float* vnode;         // [P] lumped volume of each particle (sum of V / 4)
   const unsigned char* fixed; // [P]
   const unsigned short* coff; // [P + 1] first slot of each particle's list
-  const unsigned short* csr;  // [nnz] contribution slots in ascending order
+  const unsigned short* csr;  // [nnz] contribution offsets (component 0) in slot order
   const FemLinkParams* prm;   // [links]
   float* x;                   // [links][P][3]
   float* v;                   // [links][P][3]
   float* resid;               // [links]
   int* mv;                    // [links]
-  int P, NT, ND, nnz;
+  int P, NT, ND, nnz, S;       // S = max(NT, ND): stride of the contribution components
   long long frame;
   double dt;
   int n_sub, K, pcr_iters;
@@ -182,8 +184,10 @@ __device__ __forceinline__ bool polar_rotation(const float (&F)[9], float (&R)[9
 }
 
 // Contribution slots of one element for a Voigt vector v: c_a = R Sigma(v) g_a (a = 1..3),
-// c_0 = -(c_1 + c_2 + c_3).
-__device__ __forceinline__ void tet_scatter(const float (&R)[9], const float* g, const float (&v)[6], float* cont) {
+// c_0 = -(c_1 + c_2 + c_3); component k of vertex a at cont[(3 a + k) S] (consecutive
+// elements are consecutive words: no bank conflicts).
+__device__ __forceinline__ void tet_scatter(const float (&R)[9], const float* g, const float (&v)[6], float* cont,
+                                            int S) {
   const float s00 = v[0], s11 = v[1], s22 = v[2], s12 = 0.5f * v[3], s02 = 0.5f * v[4], s01 = 0.5f * v[5];
   float t0x = 0.f, t0y = 0.f, t0z = 0.f;
 #pragma unroll
@@ -195,19 +199,20 @@ __device__ __forceinline__ void tet_scatter(const float (&R)[9], const float* g,
     const float cx = R[0] * sx + R[1] * sy + R[2] * sz;
     const float cy = R[3] * sx + R[4] * sy + R[5] * sz;
     const float cz = R[6] * sx + R[7] * sy + R[8] * sz;
-    cont[3 * (a + 1)] = cx;
-    cont[3 * (a + 1) + 1] = cy;
-    cont[3 * (a + 1) + 2] = cz;
+    cont[(3 * (a + 1)) * S] = cx;
+    cont[(3 * (a + 1) + 1) * S] = cy;
+    cont[(3 * (a + 1) + 2) * S] = cz;
     t0x += cx; t0y += cy; t0z += cz;
   }
   cont[0] = -t0x;
-  cont[1] = -t0y;
-  cont[2] = -t0z;
+  cont[S] = -t0y;
+  cont[2 * S] = -t0z;
 }
 
 // Element rows of J u: Voigt(sym(R^T H)), H = sum_{a=1..3} (u_a - u_0) g_a^T.
-__device__ __forceinline__ void tet_rows(const float (&R)[9], const float* g, const float* uu,
-                                         const unsigned short* ids, float (&y)[6]) {
+__device__ __forceinline__ void tet_rows(const float (&R)[9], const float* g, const float* uu, ushort4 id4,
+                                         float (&y)[6]) {
+  const int ids[4] = {id4.x, id4.y, id4.z, id4.w};
   const float u0x = uu[3 * ids[0]], u0y = uu[3 * ids[0] + 1], u0z = uu[3 * ids[0] + 2];
   float H[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll
@@ -257,7 +262,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) fem_frame_kernel(FemArgs A) {
 
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int link = blockIdx.x;
-  const int P = A.P, NT = A.NT, ND = A.ND;
+  const int P = A.P, NT = A.NT, ND = A.ND, S = A.S;
   const FemLinkParams pr = A.prm[link];
   const float Y = pr.youngs, nu = pr.poisson;
 
@@ -295,26 +300,47 @@ __global__ void __launch_bounds__(kMaxThreads, 1) fem_frame_kernel(FemArgs A) {
         float vin[6];
 #pragma unroll
         for (int k = 0; k < 6; ++k) vin[k] = elements_from_dl ? dl[s][k] : z[s][k];
-        tet_scatter(R[s], gS + 9 * t, vin, cont + 12 * t);
+        tet_scatter(R[s], gS + 9 * t, vin, cont + t, S);
       }
     }
     for (int d = tid; d < ND; d += nthr) {
       const float vd = elements_from_dl ? ddl[d] : dz[d];
-      float* c = cont + 12 * NT + 6 * d;
+      float* c = cont + 12 * S + d;
       const float nx = dn[3 * d] * vd, ny = dn[3 * d + 1] * vd, nz = dn[3 * d + 2] * vd;
-      c[0] = -nx; c[1] = -ny; c[2] = -nz;
-      c[3] = nx; c[4] = ny; c[5] = nz;
+      c[0] = -nx; c[S] = -ny; c[2 * S] = -nz;
+      c[3 * S] = nx; c[4 * S] = ny; c[5 * S] = nz;
     }
     __syncthreads();
-    // B: particle sums, times the inverse mass
-    for (int i = tid; i < P; i += nthr) {
+    // B: particle sums, times the inverse mass.  With at least two threads per particle,
+    // threads 2i and 2i+1 each add one half of particle i's list (first half + second
+    // half, a fixed order); otherwise one thread adds the whole list.
+    if (2 * P <= nthr) {
+      const int i = tid >> 1;
       float sx = 0.f, sy = 0.f, sz = 0.f;
-      for (int e = coff[i]; e < coff[i + 1]; ++e) {
-        const float* c = cont + 3 * csr[e];
-        sx += c[0]; sy += c[1]; sz += c[2];
+      if (i < P) {
+        const int b = coff[i], e1 = coff[i + 1], mid = b + (e1 - b + 1) / 2;
+        for (int e = (tid & 1) ? mid : b; e < ((tid & 1) ? e1 : mid); ++e) {
+          const float* c = cont + csr[e];
+          sx += c[0]; sy += c[S]; sz += c[2 * S];
+        }
       }
-      const float w = wn[i];
-      uu[3 * i] = w * sx; uu[3 * i + 1] = w * sy; uu[3 * i + 2] = w * sz;
+      sx += __shfl_xor_sync(0xffffffffu, sx, 1);
+      sy += __shfl_xor_sync(0xffffffffu, sy, 1);
+      sz += __shfl_xor_sync(0xffffffffu, sz, 1);
+      if (i < P && (tid & 1) == 0) {
+        const float w = wn[i];
+        uu[3 * i] = w * sx; uu[3 * i + 1] = w * sy; uu[3 * i + 2] = w * sz;
+      }
+    } else {
+      for (int i = tid; i < P; i += nthr) {
+        float sx = 0.f, sy = 0.f, sz = 0.f;
+        for (int e = coff[i]; e < coff[i + 1]; ++e) {
+          const float* c = cont + csr[e];
+          sx += c[0]; sy += c[S]; sz += c[2 * S];
+        }
+        const float w = wn[i];
+        uu[3 * i] = w * sx; uu[3 * i + 1] = w * sy; uu[3 * i + 2] = w * sz;
+      }
     }
     __syncthreads();
   };
@@ -325,7 +351,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) fem_frame_kernel(FemArgs A) {
       const int t = tid + s * nthr;
       if (t < NT) {
         float y[6], cz[6];
-        tet_rows(R[s], gS + 9 * t, uu, tetS + 4 * t, y);
+        tet_rows(R[s], gS + 9 * t, uu, reinterpret_cast<const ushort4*>(tetS)[t], y);
         compliance(nu, z[s], cz);
         const float sc = 1.f / (volS[t] * Y * h2);
 #pragma unroll
@@ -386,7 +412,8 @@ __global__ void __launch_bounds__(kMaxThreads, 1) fem_frame_kernel(FemArgs A) {
       for (int s = 0; s < kTPT; ++s) {
         const int t = tid + s * nthr;
         if (t < NT) {
-          const unsigned short* id = tetS + 4 * t;
+          const ushort4 id4 = reinterpret_cast<const ushort4*>(tetS)[t];  // one 8-byte load
+          const int id[4] = {id4.x, id4.y, id4.z, id4.w};
           const float* g = gS + 9 * t;
           const float x0 = xx[3 * id[0]], y0 = xx[3 * id[0] + 1], z0 = xx[3 * id[0] + 2];
           float F[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
@@ -410,7 +437,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) fem_frame_kernel(FemArgs A) {
                               0.5f * (M[1] + M[3])};
           float lam6[6], al[6];
 #pragma unroll
-          for (int k = 0; k < 6; ++k) lam6[k] = lamT[6 * t + k];
+          for (int k = 0; k < 6; ++k) lam6[k] = lamT[k * NT + t];
           compliance(nu, lam6, al);
           const float sc = 1.f / (volS[t] * Y * h2);
           // diagonal: sum_a w_a |Sigma_k g_a|^2 + sc C_kk
@@ -435,7 +462,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) fem_frame_kernel(FemArgs A) {
           for (int k = 0; k < 6; ++k) {
             const float Ckk = k < 3 ? 1.f : 1.f + nu;
             const float inv = 1.f / (dg[k] + sc * Ckk);
-            idT[6 * t + k] = inv;
+            idT[k * NT + t] = inv;
             const float b = -(c[k] + sc * al[k]);
             rloc = fmaxf(rloc, fin_or_inf(fabsf(b)));
             z[s][k] = b * inv;
@@ -485,7 +512,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) fem_frame_kernel(FemArgs A) {
           const int t = tid + s * nthr;
           if (t < NT)
 #pragma unroll
-            for (int k = 0; k < 6; ++k) qs += q[s][k] * q[s][k] * idT[6 * t + k];
+            for (int k = 0; k < 6; ++k) qs += q[s][k] * q[s][k] * idT[k * NT + t];
         }
         for (int d = tid; d < ND; d += nthr) qs += dq[d] * dq[d] * did[d];
         qs = block_sum(qs, red, nred);
@@ -498,7 +525,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) fem_frame_kernel(FemArgs A) {
 #pragma unroll
             for (int k = 0; k < 6; ++k) {
               dl[s][k] += alpha * p[s][k];
-              z[s][k] -= alpha * q[s][k] * idT[6 * t + k];
+              z[s][k] -= alpha * q[s][k] * idT[k * NT + t];
             }
         }
         for (int d = tid; d < ND; d += nthr) {
@@ -539,7 +566,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) fem_frame_kernel(FemArgs A) {
         const int t = tid + s * nthr;
         if (t < NT)
 #pragma unroll
-          for (int k = 0; k < 6; ++k) lamT[6 * t + k] += dl[s][k];
+          for (int k = 0; k < 6; ++k) lamT[k * NT + t] += dl[s][k];
       }
       for (int d = tid; d < ND; d += nthr) dlam[d] += ddl[d];
       product(true);  // (as above: the last reduction's barrier separates the reads of uu)
@@ -597,14 +624,14 @@ __global__ void fem_rest_rows_kernel(const double* X, const int* rows, int ND, f
 
 // Lumped volume of each particle: the sum of V / 4 over its element slots, in slot order.
 __global__ void fem_node_volume_kernel(const double* X, const int* tets, const unsigned short* coff,
-                                       const unsigned short* csr, int P, int NT, float* vnode) {
+                                       const unsigned short* csr, int P, int S, float* vnode) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= P) return;
   double s = 0.0;
   for (int e = coff[i]; e < coff[i + 1]; ++e) {
-    const int slot = csr[e];
-    if (slot >= 4 * NT) continue;
-    const int* id = tets + 4 * (slot / 4);
+    const int off = csr[e];
+    if (off >= 12 * S) continue;  // a distance row's end
+    const int* id = tets + 4 * (off % S);
     double D[9];
     for (int a = 0; a < 3; ++a)
       for (int k = 0; k < 3; ++k) D[3 * k + a] = X[3 * id[a + 1] + k] - X[3 * id[0] + k];
@@ -619,7 +646,7 @@ __global__ void fem_node_volume_kernel(const double* X, const int* tets, const u
 
 struct FemHandle {
   cudaStream_t st = nullptr;
-  int n_links = 0, P = 0, NT = 0, ND = 0, nnz = 0, nthr = 0;
+  int n_links = 0, P = 0, NT = 0, ND = 0, nnz = 0, S = 0, nthr = 0;
   size_t smem = 0;
   FemConfig cfg{};
   long long frame = 0, launches = 0;
@@ -705,9 +732,11 @@ SimStatus fem_create(const FemConfig* cfg, const FemMesh* mesh, int n_links, con
                                    " (Y > 0, 0 <= nu < 0.5, density > 0, damping >= 0, compliances >= 0, "
                                    "amplitude >= 0)");
   }
-  // contribution slots of each particle, ascending: element e vertex a -> 4 e + a; distance
-  // row d end k -> 4 NT + 2 d + k
+  // contribution slots of each particle in ascending slot order (element e vertex a: slot
+  // 4 e + a, offset 3 a S + e; distance row d end k: slot 4 NT + 2 d + k, offset
+  // (12 + 3 k) S + d), stored as offsets of component 0
   const int nnz = 4 * NT + 2 * ND;
+  const int S = NT > ND ? NT : ND;
   std::vector<int> cnt(P + 1, 0);
   for (int t = 0; t < NT; ++t)
     for (int a = 0; a < 4; ++a) ++cnt[mesh->tets[4 * t + a] + 1];
@@ -717,9 +746,9 @@ SimStatus fem_create(const FemConfig* cfg, const FemMesh* mesh, int n_links, con
   for (int i = 0; i <= P; ++i) coff[i] = (unsigned short)cnt[i];
   std::vector<int> pos(cnt.begin(), cnt.end() - 1);
   for (int t = 0; t < NT; ++t)
-    for (int a = 0; a < 4; ++a) csr[pos[mesh->tets[4 * t + a]]++] = (unsigned short)(4 * t + a);
+    for (int a = 0; a < 4; ++a) csr[pos[mesh->tets[4 * t + a]]++] = (unsigned short)(3 * a * S + t);
   for (int d = 0; d < ND; ++d)
-    for (int k = 0; k < 2; ++k) csr[pos[mesh->rows[2 * d + k]]++] = (unsigned short)(4 * NT + 2 * d + k);
+    for (int k = 0; k < 2; ++k) csr[pos[mesh->rows[2 * d + k]]++] = (unsigned short)((12 + 3 * k) * S + d);
   // launch shape and shared memory
   const int nthr = ((NT + kTPT - 1) / kTPT + 31) / 32 * 32;
   const FemLayout lay(P, NT, ND, nnz);
@@ -733,7 +762,7 @@ SimStatus fem_create(const FemConfig* cfg, const FemMesh* mesh, int n_links, con
 
   FemHandle* h = new FemHandle();
   h->st = (cudaStream_t)stream;
-  h->n_links = n_links; h->P = P; h->NT = NT; h->ND = ND; h->nnz = nnz; h->nthr = nthr; h->smem = lay.bytes;
+  h->n_links = n_links; h->P = P; h->NT = NT; h->ND = ND; h->nnz = nnz; h->S = S; h->nthr = nthr; h->smem = lay.bytes;
   h->cfg = *cfg;
   auto cleanup = [&](SimStatus st) {
     free_all(h);
@@ -807,7 +836,7 @@ SimStatus fem_create(const FemConfig* cfg, const FemMesh* mesh, int n_links, con
       fem_rest_rows_kernel<<<(ND + 127) / 128, 128, 0, h->st>>>(dX, dR, ND, h->rest);
       if ((e = cudaGetLastError())) break;
     }
-    fem_node_volume_kernel<<<(P + 127) / 128, 128, 0, h->st>>>(dX, dT, h->coff, h->csr, P, NT, h->vnode);
+    fem_node_volume_kernel<<<(P + 127) / 128, 128, 0, h->st>>>(dX, dT, h->coff, h->csr, P, S, h->vnode);
     if ((e = cudaGetLastError())) break;
     e = cudaStreamSynchronize(h->st);  // host staging vectors go out of scope
   } while (0);
@@ -834,7 +863,7 @@ SimStatus fem_step(FemHandle* h, int n_frames) {
   A.g = h->g; A.vol = h->vol; A.tet = h->tet; A.row = h->row; A.kind = h->kind; A.rest = h->rest;
   A.vnode = h->vnode; A.fixed = h->fixed; A.coff = h->coff; A.csr = h->csr; A.prm = h->prm;
   A.x = h->x; A.v = h->v; A.resid = h->resid; A.mv = h->mv;
-  A.P = h->P; A.NT = h->NT; A.ND = h->ND; A.nnz = h->nnz;
+  A.P = h->P; A.NT = h->NT; A.ND = h->ND; A.nnz = h->nnz; A.S = h->S;
   A.dt = h->cfg.dt; A.n_sub = h->cfg.n_sub; A.K = h->cfg.iters; A.pcr_iters = h->cfg.pcr_iters;
   A.tol = h->cfg.tol; A.gx = h->cfg.gravity[0]; A.gy = h->cfg.gravity[1]; A.gz = h->cfg.gravity[2];
   for (int f = 0; f < n_frames; ++f) {
