@@ -48,8 +48,9 @@ SimStatus ffail(SimStatus s, const std::string& msg) {
 
 // Offsets (in elements of each type) of the shared-memory areas of one block.
 struct FemLayout {
-  // floats (per-element arrays component-major: [component][element], so consecutive
-  // threads touch consecutive words)
+  // floats (per-element and per-row records padded to an odd number of words: 13 per
+  // element's contribution slots, 7 per element's multipliers / inverse diagonals, 7 per
+  // distance row's slots, so that consecutive threads hit distinct banks)
   int g, vol, lam, idg, cont, xs, xx, vv, uu, wn, dn, drest, dat, did, dlam, ddl, dz, dp, dq, daz, red, n_float;
   // unsigned shorts (after the floats)
   int tet, row, coff, csr, n_short;
@@ -60,9 +61,9 @@ struct FemLayout {
     int o = 0;
     g = o; o += NT * 9;
     vol = o; o += NT;
-    lam = o; o += NT * 6;
-    idg = o; o += NT * 6;
-    cont = o; o += 18 * (NT > ND ? NT : ND);  // [18][S]: element vertex a comp k at 3a + k, row end e at 12 + 3e + k
+    lam = o; o += NT * 7;
+    idg = o; o += NT * 7;
+    cont = o; o += 13 * NT + 7 * ND;  // element e vertex a comp k at 13 e + 3 a + k; row d end k at 13 NT + 7 d + 3 k
     xs = o; o += P * 3;
     xx = o; o += P * 3;
     vv = o; o += P * 3;
@@ -112,7 +113,7 @@ struct FemArgs {
   float* v;                   // [links][P][3]
   float* resid;               // [links]
   int* mv;                    // [links]
-  int P, NT, ND, nnz, S;       // S = max(NT, ND): stride of the contribution components
+  int P, NT, ND, nnz;
   long long frame;
   double dt;
   int n_sub, K, pcr_iters;
@@ -122,8 +123,8 @@ struct FemArgs {
 
 __device__ __forceinline__ float fin_or_inf(float a) { return (a <= 3.0e38f) ? a : INFINITY; }
 
-// Sum / maximum over the block; every thread gets the same value (partials combined in
-// warp order).  Consecutive reductions alternate between two halves of `red`, so one
+// Sum / maximum over the block; every thread gets the same value (the per-warp partials
+// combined by the same butterfly in every warp).  Consecutive reductions alternate between two halves of `red`, so one
 // barrier per reduction suffices: a half is rewritten two reductions later, after every
 // thread has passed the barrier of the reduction in between.
 __device__ __forceinline__ float block_sum(float a, float* red, int& k) {
@@ -134,8 +135,9 @@ __device__ __forceinline__ float block_sum(float a, float* red, int& k) {
   ++k;
   if ((threadIdx.x & 31) == 0) r[w] = a;
   __syncthreads();
-  float s = 0.f;
-  for (int i = 0; i < nw; ++i) s += r[i];
+  float s = (threadIdx.x & 31) < nw ? r[threadIdx.x & 31] : 0.f;
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   return s;
 }
 
@@ -147,8 +149,9 @@ __device__ __forceinline__ float block_max(float a, float* red, int& k) {
   ++k;
   if ((threadIdx.x & 31) == 0) r[w] = a;
   __syncthreads();
-  float s = 0.f;
-  for (int i = 0; i < nw; ++i) s = fmaxf(s, r[i]);
+  float s = (threadIdx.x & 31) < nw ? r[threadIdx.x & 31] : 0.f;
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) s = fmaxf(s, __shfl_xor_sync(0xffffffffu, s, o));
   return s;
 }
 
@@ -184,10 +187,8 @@ __device__ __forceinline__ bool polar_rotation(const float (&F)[9], float (&R)[9
 }
 
 // Contribution slots of one element for a Voigt vector v: c_a = R Sigma(v) g_a (a = 1..3),
-// c_0 = -(c_1 + c_2 + c_3); component k of vertex a at cont[(3 a + k) S] (consecutive
-// elements are consecutive words: no bank conflicts).
-__device__ __forceinline__ void tet_scatter(const float (&R)[9], const float* g, const float (&v)[6], float* cont,
-                                            int S) {
+// c_0 = -(c_1 + c_2 + c_3), vertex a's three components at cont[3 a].
+__device__ __forceinline__ void tet_scatter(const float (&R)[9], const float* g, const float (&v)[6], float* cont) {
   const float s00 = v[0], s11 = v[1], s22 = v[2], s12 = 0.5f * v[3], s02 = 0.5f * v[4], s01 = 0.5f * v[5];
   float t0x = 0.f, t0y = 0.f, t0z = 0.f;
 #pragma unroll
@@ -199,14 +200,14 @@ __device__ __forceinline__ void tet_scatter(const float (&R)[9], const float* g,
     const float cx = R[0] * sx + R[1] * sy + R[2] * sz;
     const float cy = R[3] * sx + R[4] * sy + R[5] * sz;
     const float cz = R[6] * sx + R[7] * sy + R[8] * sz;
-    cont[(3 * (a + 1)) * S] = cx;
-    cont[(3 * (a + 1) + 1) * S] = cy;
-    cont[(3 * (a + 1) + 2) * S] = cz;
+    cont[3 * (a + 1)] = cx;
+    cont[3 * (a + 1) + 1] = cy;
+    cont[3 * (a + 1) + 2] = cz;
     t0x += cx; t0y += cy; t0z += cz;
   }
   cont[0] = -t0x;
-  cont[S] = -t0y;
-  cont[2 * S] = -t0z;
+  cont[1] = -t0y;
+  cont[2] = -t0z;
 }
 
 // Element rows of J u: Voigt(sym(R^T H)), H = sum_{a=1..3} (u_a - u_0) g_a^T.
@@ -262,7 +263,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) fem_frame_kernel(FemArgs A) {
 
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int link = blockIdx.x;
-  const int P = A.P, NT = A.NT, ND = A.ND, S = A.S;
+  const int P = A.P, NT = A.NT, ND = A.ND;
   const FemLinkParams pr = A.prm[link];
   const float Y = pr.youngs, nu = pr.poisson;
 
@@ -300,15 +301,15 @@ __global__ void __launch_bounds__(kMaxThreads, 1) fem_frame_kernel(FemArgs A) {
         float vin[6];
 #pragma unroll
         for (int k = 0; k < 6; ++k) vin[k] = elements_from_dl ? dl[s][k] : z[s][k];
-        tet_scatter(R[s], gS + 9 * t, vin, cont + t, S);
+        tet_scatter(R[s], gS + 9 * t, vin, cont + 13 * t);
       }
     }
     for (int d = tid; d < ND; d += nthr) {
       const float vd = elements_from_dl ? ddl[d] : dz[d];
-      float* c = cont + 12 * S + d;
+      float* c = cont + 13 * NT + 7 * d;
       const float nx = dn[3 * d] * vd, ny = dn[3 * d + 1] * vd, nz = dn[3 * d + 2] * vd;
-      c[0] = -nx; c[S] = -ny; c[2 * S] = -nz;
-      c[3 * S] = nx; c[4 * S] = ny; c[5 * S] = nz;
+      c[0] = -nx; c[1] = -ny; c[2] = -nz;
+      c[3] = nx; c[4] = ny; c[5] = nz;
     }
     __syncthreads();
     // B: particle sums, times the inverse mass.  With at least two threads per particle,
@@ -321,7 +322,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) fem_frame_kernel(FemArgs A) {
         const int b = coff[i], e1 = coff[i + 1], mid = b + (e1 - b + 1) / 2;
         for (int e = (tid & 1) ? mid : b; e < ((tid & 1) ? e1 : mid); ++e) {
           const float* c = cont + csr[e];
-          sx += c[0]; sy += c[S]; sz += c[2 * S];
+          sx += c[0]; sy += c[1]; sz += c[2];
         }
       }
       sx += __shfl_xor_sync(0xffffffffu, sx, 1);
@@ -336,7 +337,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) fem_frame_kernel(FemArgs A) {
         float sx = 0.f, sy = 0.f, sz = 0.f;
         for (int e = coff[i]; e < coff[i + 1]; ++e) {
           const float* c = cont + csr[e];
-          sx += c[0]; sy += c[S]; sz += c[2 * S];
+          sx += c[0]; sy += c[1]; sz += c[2];
         }
         const float w = wn[i];
         uu[3 * i] = w * sx; uu[3 * i + 1] = w * sy; uu[3 * i + 2] = w * sz;
@@ -400,7 +401,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) fem_frame_kernel(FemArgs A) {
       drest[d] = (kd == FEM_ROW_ACT_LEFT || kd == FEM_ROW_ACT_RIGHT) ? A.rest[d] * eps : A.rest[d];
       dlam[d] = 0.f;
     }
-    for (int i = tid; i < NT * 6; i += nthr) lamT[i] = 0.f;
+    for (int i = tid; i < NT * 7; i += nthr) lamT[i] = 0.f;
     __syncthreads();
 
     int mv = 0;
@@ -437,7 +438,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) fem_frame_kernel(FemArgs A) {
                               0.5f * (M[1] + M[3])};
           float lam6[6], al[6];
 #pragma unroll
-          for (int k = 0; k < 6; ++k) lam6[k] = lamT[k * NT + t];
+          for (int k = 0; k < 6; ++k) lam6[k] = lamT[7 * t + k];
           compliance(nu, lam6, al);
           const float sc = 1.f / (volS[t] * Y * h2);
           // diagonal: sum_a w_a |Sigma_k g_a|^2 + sc C_kk
@@ -462,7 +463,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) fem_frame_kernel(FemArgs A) {
           for (int k = 0; k < 6; ++k) {
             const float Ckk = k < 3 ? 1.f : 1.f + nu;
             const float inv = 1.f / (dg[k] + sc * Ckk);
-            idT[k * NT + t] = inv;
+            idT[7 * t + k] = inv;
             const float b = -(c[k] + sc * al[k]);
             rloc = fmaxf(rloc, fin_or_inf(fabsf(b)));
             z[s][k] = b * inv;
@@ -512,7 +513,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) fem_frame_kernel(FemArgs A) {
           const int t = tid + s * nthr;
           if (t < NT)
 #pragma unroll
-            for (int k = 0; k < 6; ++k) qs += q[s][k] * q[s][k] * idT[k * NT + t];
+            for (int k = 0; k < 6; ++k) qs += q[s][k] * q[s][k] * idT[7 * t + k];
         }
         for (int d = tid; d < ND; d += nthr) qs += dq[d] * dq[d] * did[d];
         qs = block_sum(qs, red, nred);
@@ -525,7 +526,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) fem_frame_kernel(FemArgs A) {
 #pragma unroll
             for (int k = 0; k < 6; ++k) {
               dl[s][k] += alpha * p[s][k];
-              z[s][k] -= alpha * q[s][k] * idT[k * NT + t];
+              z[s][k] -= alpha * q[s][k] * idT[7 * t + k];
             }
         }
         for (int d = tid; d < ND; d += nthr) {
@@ -566,7 +567,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) fem_frame_kernel(FemArgs A) {
         const int t = tid + s * nthr;
         if (t < NT)
 #pragma unroll
-          for (int k = 0; k < 6; ++k) lamT[k * NT + t] += dl[s][k];
+          for (int k = 0; k < 6; ++k) lamT[7 * t + k] += dl[s][k];
       }
       for (int d = tid; d < ND; d += nthr) dlam[d] += ddl[d];
       product(true);  // (as above: the last reduction's barrier separates the reads of uu)
@@ -624,14 +625,14 @@ __global__ void fem_rest_rows_kernel(const double* X, const int* rows, int ND, f
 
 // Lumped volume of each particle: the sum of V / 4 over its element slots, in slot order.
 __global__ void fem_node_volume_kernel(const double* X, const int* tets, const unsigned short* coff,
-                                       const unsigned short* csr, int P, int S, float* vnode) {
+                                       const unsigned short* csr, int P, int NT, float* vnode) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= P) return;
   double s = 0.0;
   for (int e = coff[i]; e < coff[i + 1]; ++e) {
     const int off = csr[e];
-    if (off >= 12 * S) continue;  // a distance row's end
-    const int* id = tets + 4 * (off % S);
+    if (off >= 13 * NT) continue;  // a distance row's end
+    const int* id = tets + 4 * (off / 13);
     double D[9];
     for (int a = 0; a < 3; ++a)
       for (int k = 0; k < 3; ++k) D[3 * k + a] = X[3 * id[a + 1] + k] - X[3 * id[0] + k];
@@ -646,7 +647,7 @@ __global__ void fem_node_volume_kernel(const double* X, const int* tets, const u
 
 struct FemHandle {
   cudaStream_t st = nullptr;
-  int n_links = 0, P = 0, NT = 0, ND = 0, nnz = 0, S = 0, nthr = 0;
+  int n_links = 0, P = 0, NT = 0, ND = 0, nnz = 0, nthr = 0;
   size_t smem = 0;
   FemConfig cfg{};
   long long frame = 0, launches = 0;
@@ -733,10 +734,9 @@ SimStatus fem_create(const FemConfig* cfg, const FemMesh* mesh, int n_links, con
                                    "amplitude >= 0)");
   }
   // contribution slots of each particle in ascending slot order (element e vertex a: slot
-  // 4 e + a, offset 3 a S + e; distance row d end k: slot 4 NT + 2 d + k, offset
-  // (12 + 3 k) S + d), stored as offsets of component 0
+  // 4 e + a, offset 13 e + 3 a; distance row d end k: slot 4 NT + 2 d + k, offset
+  // 13 NT + 7 d + 3 k), stored as offsets of component 0
   const int nnz = 4 * NT + 2 * ND;
-  const int S = NT > ND ? NT : ND;
   std::vector<int> cnt(P + 1, 0);
   for (int t = 0; t < NT; ++t)
     for (int a = 0; a < 4; ++a) ++cnt[mesh->tets[4 * t + a] + 1];
@@ -746,9 +746,9 @@ SimStatus fem_create(const FemConfig* cfg, const FemMesh* mesh, int n_links, con
   for (int i = 0; i <= P; ++i) coff[i] = (unsigned short)cnt[i];
   std::vector<int> pos(cnt.begin(), cnt.end() - 1);
   for (int t = 0; t < NT; ++t)
-    for (int a = 0; a < 4; ++a) csr[pos[mesh->tets[4 * t + a]]++] = (unsigned short)(3 * a * S + t);
+    for (int a = 0; a < 4; ++a) csr[pos[mesh->tets[4 * t + a]]++] = (unsigned short)(13 * t + 3 * a);
   for (int d = 0; d < ND; ++d)
-    for (int k = 0; k < 2; ++k) csr[pos[mesh->rows[2 * d + k]]++] = (unsigned short)((12 + 3 * k) * S + d);
+    for (int k = 0; k < 2; ++k) csr[pos[mesh->rows[2 * d + k]]++] = (unsigned short)(13 * NT + 7 * d + 3 * k);
   // launch shape and shared memory
   const int nthr = ((NT + kTPT - 1) / kTPT + 31) / 32 * 32;
   const FemLayout lay(P, NT, ND, nnz);
@@ -762,7 +762,7 @@ SimStatus fem_create(const FemConfig* cfg, const FemMesh* mesh, int n_links, con
 
   FemHandle* h = new FemHandle();
   h->st = (cudaStream_t)stream;
-  h->n_links = n_links; h->P = P; h->NT = NT; h->ND = ND; h->nnz = nnz; h->S = S; h->nthr = nthr; h->smem = lay.bytes;
+  h->n_links = n_links; h->P = P; h->NT = NT; h->ND = ND; h->nnz = nnz; h->nthr = nthr; h->smem = lay.bytes;
   h->cfg = *cfg;
   auto cleanup = [&](SimStatus st) {
     free_all(h);
@@ -836,7 +836,7 @@ SimStatus fem_create(const FemConfig* cfg, const FemMesh* mesh, int n_links, con
       fem_rest_rows_kernel<<<(ND + 127) / 128, 128, 0, h->st>>>(dX, dR, ND, h->rest);
       if ((e = cudaGetLastError())) break;
     }
-    fem_node_volume_kernel<<<(P + 127) / 128, 128, 0, h->st>>>(dX, dT, h->coff, h->csr, P, S, h->vnode);
+    fem_node_volume_kernel<<<(P + 127) / 128, 128, 0, h->st>>>(dX, dT, h->coff, h->csr, P, NT, h->vnode);
     if ((e = cudaGetLastError())) break;
     e = cudaStreamSynchronize(h->st);  // host staging vectors go out of scope
   } while (0);
@@ -863,7 +863,7 @@ SimStatus fem_step(FemHandle* h, int n_frames) {
   A.g = h->g; A.vol = h->vol; A.tet = h->tet; A.row = h->row; A.kind = h->kind; A.rest = h->rest;
   A.vnode = h->vnode; A.fixed = h->fixed; A.coff = h->coff; A.csr = h->csr; A.prm = h->prm;
   A.x = h->x; A.v = h->v; A.resid = h->resid; A.mv = h->mv;
-  A.P = h->P; A.NT = h->NT; A.ND = h->ND; A.nnz = h->nnz; A.S = h->S;
+  A.P = h->P; A.NT = h->NT; A.ND = h->ND; A.nnz = h->nnz;
   A.dt = h->cfg.dt; A.n_sub = h->cfg.n_sub; A.K = h->cfg.iters; A.pcr_iters = h->cfg.pcr_iters;
   A.tol = h->cfg.tol; A.gx = h->cfg.gravity[0]; A.gy = h->cfg.gravity[1]; A.gz = h->cfg.gravity[2];
   for (int f = 0; f < n_frames; ++f) {
