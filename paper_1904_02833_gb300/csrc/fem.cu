@@ -210,6 +210,28 @@ __device__ __forceinline__ void tet_scatter(const float (&R)[9], const float* g,
   cont[2] = -t0z;
 }
 
+// Adds the contribution slots csr[lo..hi) in order; the offsets of four slots are read
+// before their values, so the dependent shared-memory loads overlap.
+__device__ __forceinline__ void slot_sum(const float* cont, const unsigned short* csr, int lo, int hi, float& sx,
+                                         float& sy, float& sz) {
+  int e = lo;
+  for (; e + 4 <= hi; e += 4) {
+    const int o0 = csr[e], o1 = csr[e + 1], o2 = csr[e + 2], o3 = csr[e + 3];
+    const float a0 = cont[o0], b0 = cont[o0 + 1], c0 = cont[o0 + 2];
+    const float a1 = cont[o1], b1 = cont[o1 + 1], c1 = cont[o1 + 2];
+    const float a2 = cont[o2], b2 = cont[o2 + 1], c2 = cont[o2 + 2];
+    const float a3 = cont[o3], b3 = cont[o3 + 1], c3 = cont[o3 + 2];
+    sx += a0; sy += b0; sz += c0;
+    sx += a1; sy += b1; sz += c1;
+    sx += a2; sy += b2; sz += c2;
+    sx += a3; sy += b3; sz += c3;
+  }
+  for (; e < hi; ++e) {
+    const float* c = cont + csr[e];
+    sx += c[0]; sy += c[1]; sz += c[2];
+  }
+}
+
 // Element rows of J u: Voigt(sym(R^T H)), H = sum_{a=1..3} (u_a - u_0) g_a^T.
 __device__ __forceinline__ void tet_rows(const float (&R)[9], const float* g, const float* uu, ushort4 id4,
                                          float (&y)[6]) {
@@ -320,10 +342,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) fem_frame_kernel(FemArgs A) {
       float sx = 0.f, sy = 0.f, sz = 0.f;
       if (i < P) {
         const int b = coff[i], e1 = coff[i + 1], mid = b + (e1 - b + 1) / 2;
-        for (int e = (tid & 1) ? mid : b; e < ((tid & 1) ? e1 : mid); ++e) {
-          const float* c = cont + csr[e];
-          sx += c[0]; sy += c[1]; sz += c[2];
-        }
+        slot_sum(cont, csr, (tid & 1) ? mid : b, (tid & 1) ? e1 : mid, sx, sy, sz);
       }
       sx += __shfl_xor_sync(0xffffffffu, sx, 1);
       sy += __shfl_xor_sync(0xffffffffu, sy, 1);
@@ -335,10 +354,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) fem_frame_kernel(FemArgs A) {
     } else {
       for (int i = tid; i < P; i += nthr) {
         float sx = 0.f, sy = 0.f, sz = 0.f;
-        for (int e = coff[i]; e < coff[i + 1]; ++e) {
-          const float* c = cont + csr[e];
-          sx += c[0]; sy += c[1]; sz += c[2];
-        }
+        slot_sum(cont, csr, coff[i], coff[i + 1], sx, sy, sz);
         const float w = wn[i];
         uu[3 * i] = w * sx; uu[3 * i + 1] = w * sy; uu[3 * i + 2] = w * sz;
       }
