@@ -154,6 +154,51 @@ def test_static_sag_matches_linear_fem(nu):
     assert np.abs(got - u).max() < 2e-4 * np.abs(u).max()
 
 
+def test_static_sag_with_compliant_distance_rows():
+    """The same settling with the centre-layer and perimeter rows made compliant (alpha):
+    each adds the spring stiffness (1 / alpha) n n^T between its two particles to K."""
+    M = _small_mesh(rows=True)
+    g = (0.0, -2e-3, -1e-3)
+    a_in, a_pe = 2e-3, 5e-3
+    w = W.fem_const_pressure(1, [0.0], poisson=0.3, damping=40.0, alpha_inext=a_in, alpha_perim=a_pe)
+    s = W.fem_settings(dt=1.0 / 60.0, n_sub=1, iters=20000, tol=1e-13, pcr_iters=400, gravity=g)
+    o = F.OracleFem(M, w, s, n_threads=1)
+    for _ in range(40):
+        o.step(1)
+    X = M["X"]
+    K = _linear_fem_stiffness(M, w["youngs"][0], 0.3)
+    for (i, j), kind in zip(M["rows"], M["kinds"]):
+        if kind not in (W.FEM_INEXT, W.FEM_PERIM):
+            continue  # actuation rows do not exist at zero pressure
+        n = (X[j] - X[i]) / np.linalg.norm(X[j] - X[i])
+        k = np.outer(n, n) / (a_in if kind == W.FEM_INEXT else a_pe)
+        for a, b, sg in ((i, i, 1), (j, j, 1), (i, j, -1), (j, i, -1)):
+            K[3 * a:3 * a + 3, 3 * b:3 * b + 3] += sg * k
+    free = np.flatnonzero(M["fixed"] == 0)
+    m = _lumped_masses(M, w["density"][0])
+    dof = np.array([[3 * v, 3 * v + 1, 3 * v + 2] for v in free]).ravel()
+    f = (m[free][:, None] * np.asarray(g)[None, :]).ravel()
+    u = np.linalg.solve(K[np.ix_(dof, dof)], f).reshape(-1, 3)
+    got = o.x[0, free] - X[free]
+    assert np.abs(got - u).max() < 2e-4 * np.abs(u).max()
+    # the rows are stiff enough to matter: without them the sag differs
+    u0 = np.linalg.solve(_linear_fem_stiffness(M, w["youngs"][0], 0.3)[np.ix_(dof, dof)], f).reshape(-1, 3)
+    assert np.abs(u0 - u).max() > 0.05 * np.abs(u).max()
+
+
+def test_curvature_is_linear_in_small_pressures():
+    """Sec. VI-A: the link's curvature grows linearly with pressure in the small-strain
+    range; the settled tip deflection at 2 p is twice that at p to 1 %."""
+    M = W.fem_link_mesh(m=4, n_sec=5, length=0.05)
+    w = W.fem_const_pressure(2, [200.0, 400.0], poisson=0.3, damping=40.0)
+    s = W.fem_settings(n_sub=1, iters=20000, tol=1e-12, pcr_iters=300)
+    o = F.OracleFem(M, w, s)
+    for _ in range(40):
+        o.step(1)
+    tip = (o.x[:, -9:] - M["X"][None, -9:]).mean(1)[:, 1]
+    assert tip[0] > 0 and tip[1] / tip[0] == pytest.approx(2.0, rel=1e-2)
+
+
 def test_actuation_row_rest_length_follows_eq2():
     """One element, three vertices held, a hard actuation row from a held vertex to the
     free one: after a solved substep their distance is r (1 + |p| / Y) when that row's

@@ -69,6 +69,18 @@ def test_small_mesh_more_substeps_and_iterations():
     _check(M, w, s, frames=2)
 
 
+def test_compliant_rows_and_clamped_command():
+    """Compliant centre-layer and perimeter rows, offsets that saturate the command
+    (clamp at +-1) and a link whose command is exactly zero, over three frames."""
+    M = W.fem_link_mesh()
+    w = W.fem_links(6, seed=15)
+    w["alpha_inext"][:] = 1e-4
+    w["alpha_perim"][:] = 3e-4
+    w["press_offset"][:] = [1.5, -1.5, 0.4, -0.4, 0.0, 0.0]
+    w["press_amp"][5] = 0.0
+    _check(M, w, W.fem_settings(), frames=3)
+
+
 def test_tolerance_stops_the_newton_loop():
     M = W.fem_link_mesh(m=4, n_sec=4, length=0.04)
     w = W.fem_const_pressure(4, [3000.0, -3000.0, 6000.0, 0.0], poisson=0.3)
