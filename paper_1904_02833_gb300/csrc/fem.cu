@@ -606,10 +606,8 @@ __global__ void __launch_bounds__(kMaxThreads, 1) fem_frame_kernel(FemArgs A) {
   }
 }
 
-// Rest data of the mesh in FP64: shape-function gradients and volumes of the elements,
-// rest lengths of the distance rows.
-__global__ void fem_rest_kernel(const double* X, const int* tets, const int* rows, int NT, int ND, float* g,
-                                float* vol) {
+// Rest data of the elements in FP64: shape-function gradients and volumes.
+__global__ void fem_rest_kernel(const double* X, const int* tets, int NT, float* g, float* vol) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t < NT) {
     const int* id = tets + 4 * t;
@@ -626,10 +624,9 @@ __global__ void fem_rest_kernel(const double* X, const int* tets, const int* row
     for (int i = 0; i < 9; ++i) g[9 * t + i] = (float)B[i];
     vol[t] = (float)(det / 6.0);
   }
-  (void)rows;
-  (void)ND;
 }
 
+// Rest lengths of the distance rows in FP64.
 __global__ void fem_rest_rows_kernel(const double* X, const int* rows, int ND, float* rest) {
   const int d = blockIdx.x * blockDim.x + threadIdx.x;
   if (d < ND) {
@@ -790,11 +787,6 @@ SimStatus fem_create(const FemConfig* cfg, const FemMesh* mesh, int n_links, con
     cudaError_t e_ = cudaMalloc((void**)&(ptr), (bytes) > 0 ? (bytes) : 16);                  \
     if (e_ != cudaSuccess) return cleanup(ffail(SIM_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e_))); \
   } while (0)
-#define FCHK(call)                                                                            \
-  do {                                                                                        \
-    cudaError_t e_ = (call);                                                                  \
-    if (e_ != cudaSuccess) return cleanup(ffail(SIM_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_))); \
-  } while (0)
   const size_t nstate = (size_t)n_links * P * 3;
   FALLOC(h->g, sizeof(float) * NT * 9);
   FALLOC(h->vol, sizeof(float) * NT);
@@ -846,7 +838,7 @@ SimStatus fem_create(const FemConfig* cfg, const FemMesh* mesh, int n_links, con
     if ((e = cudaMemsetAsync(h->v, 0, sizeof(float) * nstate, h->st))) break;
     if ((e = cudaMemsetAsync(h->resid, 0, sizeof(float) * n_links, h->st))) break;
     if ((e = cudaMemsetAsync(h->mv, 0, sizeof(int) * n_links, h->st))) break;
-    fem_rest_kernel<<<(NT + 127) / 128, 128, 0, h->st>>>(dX, dT, dR, NT, ND, h->g, h->vol);
+    fem_rest_kernel<<<(NT + 127) / 128, 128, 0, h->st>>>(dX, dT, NT, h->g, h->vol);
     if ((e = cudaGetLastError())) break;
     if (ND > 0) {
       fem_rest_rows_kernel<<<(ND + 127) / 128, 128, 0, h->st>>>(dX, dR, ND, h->rest);
@@ -859,7 +851,6 @@ SimStatus fem_create(const FemConfig* cfg, const FemMesh* mesh, int n_links, con
   free_tmp();
   if (e != cudaSuccess) return cleanup(ffail(SIM_ECUDA, std::string("fem_create: ") + cudaGetErrorString(e)));
 #undef FALLOC
-#undef FCHK
   *out = h;
   return SIM_OK;
 }
