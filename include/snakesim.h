@@ -247,6 +247,14 @@ SimStatus sim_kernel_times(SimHandle* h, float* ms, int64_t* launches);
 /* Frees the handle and its device buffers (synchronises the stream).  NULL is ok. */
 SimStatus sim_destroy(SimHandle* h);
 
+/* Measures the FP32 arithmetic roof the solvers are compared against: enqueues on
+ * `stream` n_blocks blocks of 256 threads, each thread running `iters` rounds of 16 x 8
+ * independent fused multiply-adds (256 FLOP per round and thread), and writes one
+ * float per thread to out_dev (device, n_blocks * 256 floats) so that nothing is
+ * optimised away.  The caller times it (FLOP = n_blocks * 256 * iters * 256).
+ * Errors: SIM_EINVAL (n_blocks < 1, iters < 1, null out_dev), SIM_ECUDA. */
+SimStatus sim_fp32_fma_probe(float* out_dev, int n_blocks, int iters, void* stream);
+
 /* ---------------------------------------------------------------- learned warm start
  * A small network predicts the multipliers each substep starts from, so that fewer
  * Jacobi updates reach the tolerance (no counterpart in the paper, which solves every

@@ -91,6 +91,7 @@ SIGNATURES = {
     "sim_feature_offsets": [H, P],
     "sim_kernel_times": [H, P, P],
     "sim_destroy": [H],
+    "sim_fp32_fma_probe": [P, ctypes.c_int, ctypes.c_int, P],
     "sim_set_mlp": [H, H],
     "sim_snapshot_save": [H],
     "sim_calib_forward": [H, P, ctypes.c_int, ctypes.c_int, P],
