@@ -48,11 +48,9 @@ SimStatus ffail(SimStatus s, const std::string& msg) {
 
 // Offsets (in elements of each type) of the shared-memory areas of one block.
 struct FemLayout {
-  // floats, every area starting on a 16-byte boundary.  Per-element records: shape
-  // gradients and contribution slots 12 words (three 16-byte words; consecutive elements
-  // 48 bytes apart fall in distinct banks for 16-byte accesses), multipliers and inverse
-  // diagonals 7 words (odd: distinct banks for 4-byte accesses); particle sums 4 words;
-  // distance rows' slots 7 words.
+  // floats (per-element and per-row records padded to an odd number of words: 13 per
+  // element's contribution slots, 7 per element's multipliers / inverse diagonals, 7 per
+  // distance row's slots, so that consecutive threads hit distinct banks)
   int g, vol, lam, idg, cont, xs, xx, vv, uu, wn, dn, drest, dat, did, dlam, ddl, dz, dp, dq, daz, red, n_float;
   // unsigned shorts (after the floats)
   int tet, row, coff, csr, n_short;
@@ -61,29 +59,29 @@ struct FemLayout {
   size_t bytes;
   __host__ __device__ FemLayout(int P, int NT, int ND, int nnz) {
     int o = 0;
-    auto take = [&o](int n) { const int at = o; o = (o + n + 3) & ~3; return at; };
-    g = take(NT * 12);
-    vol = take(NT);
-    lam = take(NT * 7);
-    idg = take(NT * 7);
-    cont = take(12 * NT + 7 * ND);  // element e: 12 e + (vertex 1, 2, 3, 0 at 0, 3, 6, 9); row d end k: 12 NT + 7 d + 3 k
-    xs = take(P * 3);
-    xx = take(P * 3);
-    vv = take(P * 3);
-    uu = take(P * 4);
-    wn = take(P);
-    dn = take(ND * 3);
-    drest = take(ND);
-    dat = take(ND);
-    did = take(ND);
-    dlam = take(ND);
-    ddl = take(ND);
-    dz = take(ND);
-    dp = take(ND);
-    dq = take(ND);
-    daz = take(ND);
-    red = take(64);
-    n_float = o;  // a multiple of 4: the vertex ids that follow are read as 8-byte words
+    g = o; o += NT * 9;
+    vol = o; o += NT;
+    lam = o; o += NT * 7;
+    idg = o; o += NT * 7;
+    cont = o; o += 13 * NT + 7 * ND;  // element e vertex a comp k at 13 e + 3 a + k; row d end k at 13 NT + 7 d + 3 k
+    xs = o; o += P * 3;
+    xx = o; o += P * 3;
+    vv = o; o += P * 3;
+    uu = o; o += P * 3;
+    wn = o; o += P;
+    dn = o; o += ND * 3;
+    drest = o; o += ND;
+    dat = o; o += ND;
+    did = o; o += ND;
+    dlam = o; o += ND;
+    ddl = o; o += ND;
+    dz = o; o += ND;
+    dp = o; o += ND;
+    dq = o; o += ND;
+    daz = o; o += ND;
+    red = o; o += 64;
+    o = (o + 3) & ~3;  // the vertex ids that follow are read as 8-byte words
+    n_float = o;
     int s = 0;
     tet = s; s += NT * 4;
     row = s; s += ND * 2;
@@ -188,38 +186,28 @@ __device__ __forceinline__ bool polar_rotation(const float (&F)[9], float (&R)[9
   return ok;
 }
 
-// Shape-function gradients g_1, g_2, g_3 of element t (three 16-byte loads).
-__device__ __forceinline__ void load_g(const float* gS, int t, float (&g)[9]) {
-  const float4* q = reinterpret_cast<const float4*>(gS + 12 * t);
-  const float4 a = q[0], b = q[1], c = q[2];
-  g[0] = a.x; g[1] = a.y; g[2] = a.z; g[3] = a.w;
-  g[4] = b.x; g[5] = b.y; g[6] = b.z; g[7] = b.w;
-  g[8] = c.x;
-}
-
 // Contribution slots of one element for a Voigt vector v: c_a = R Sigma(v) g_a (a = 1..3),
-// c_0 = -(c_1 + c_2 + c_3), stored as three 16-byte words (c_1, c_2, c_3, c_0 in order).
-__device__ __forceinline__ void tet_scatter(const float (&R)[9], const float (&g)[9], const float (&v)[6],
-                                            float* cont) {
+// c_0 = -(c_1 + c_2 + c_3), vertex a's three components at cont[3 a].
+__device__ __forceinline__ void tet_scatter(const float (&R)[9], const float* g, const float (&v)[6], float* cont) {
   const float s00 = v[0], s11 = v[1], s22 = v[2], s12 = 0.5f * v[3], s02 = 0.5f * v[4], s01 = 0.5f * v[5];
-  float c[12];
+  float t0x = 0.f, t0y = 0.f, t0z = 0.f;
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     const float gx = g[3 * a], gy = g[3 * a + 1], gz = g[3 * a + 2];
     const float sx = s00 * gx + s01 * gy + s02 * gz;
     const float sy = s01 * gx + s11 * gy + s12 * gz;
     const float sz = s02 * gx + s12 * gy + s22 * gz;
-    c[3 * a] = R[0] * sx + R[1] * sy + R[2] * sz;
-    c[3 * a + 1] = R[3] * sx + R[4] * sy + R[5] * sz;
-    c[3 * a + 2] = R[6] * sx + R[7] * sy + R[8] * sz;
+    const float cx = R[0] * sx + R[1] * sy + R[2] * sz;
+    const float cy = R[3] * sx + R[4] * sy + R[5] * sz;
+    const float cz = R[6] * sx + R[7] * sy + R[8] * sz;
+    cont[3 * (a + 1)] = cx;
+    cont[3 * (a + 1) + 1] = cy;
+    cont[3 * (a + 1) + 2] = cz;
+    t0x += cx; t0y += cy; t0z += cz;
   }
-  c[9] = -((c[0] + c[3]) + c[6]);
-  c[10] = -((c[1] + c[4]) + c[7]);
-  c[11] = -((c[2] + c[5]) + c[8]);
-  float4* q = reinterpret_cast<float4*>(cont);
-  q[0] = make_float4(c[0], c[1], c[2], c[3]);
-  q[1] = make_float4(c[4], c[5], c[6], c[7]);
-  q[2] = make_float4(c[8], c[9], c[10], c[11]);
+  cont[0] = -t0x;
+  cont[1] = -t0y;
+  cont[2] = -t0z;
 }
 
 // Adds the contribution slots csr[lo..hi) in order; the offsets of four slots are read
@@ -245,15 +233,15 @@ __device__ __forceinline__ void slot_sum(const float* cont, const unsigned short
 }
 
 // Element rows of J u: Voigt(sym(R^T H)), H = sum_{a=1..3} (u_a - u_0) g_a^T.
-__device__ __forceinline__ void tet_rows(const float (&R)[9], const float (&g)[9], const float4* uu4, ushort4 id4,
+__device__ __forceinline__ void tet_rows(const float (&R)[9], const float* g, const float* uu, ushort4 id4,
                                          float (&y)[6]) {
   const int ids[4] = {id4.x, id4.y, id4.z, id4.w};
-  const float4 u0 = uu4[ids[0]];
+  const float u0x = uu[3 * ids[0]], u0y = uu[3 * ids[0] + 1], u0z = uu[3 * ids[0] + 2];
   float H[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    const float4 ua = uu4[ids[a + 1]];
-    const float dx = ua.x - u0.x, dy = ua.y - u0.y, dz = ua.z - u0.z;
+    const int p = ids[a + 1];
+    const float dx = uu[3 * p] - u0x, dy = uu[3 * p + 1] - u0y, dz = uu[3 * p + 2] - u0z;
     const float gx = g[3 * a], gy = g[3 * a + 1], gz = g[3 * a + 2];
     H[0] += dx * gx; H[1] += dx * gy; H[2] += dx * gz;
     H[3] += dy * gx; H[4] += dy * gy; H[5] += dy * gz;
@@ -302,8 +290,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) fem_frame_kernel(FemArgs A) {
   const float Y = pr.youngs, nu = pr.poisson;
 
   // ---- mesh and state of this link into shared memory
-  for (int i = tid; i < NT * 9; i += nthr) gS[12 * (i / 9) + i % 9] = A.g[i];
-  for (int i = tid; i < NT * 3; i += nthr) gS[12 * (i / 3) + 9 + i % 3] = 0.f;
+  for (int i = tid; i < NT * 9; i += nthr) gS[i] = A.g[i];
   for (int i = tid; i < NT; i += nthr) volS[i] = A.vol[i];
   for (int i = tid; i < NT * 4; i += nthr) tetS[i] = A.tet[i];
   for (int i = tid; i < ND * 2; i += nthr) rowS[i] = A.row[i];
@@ -336,14 +323,12 @@ __global__ void __launch_bounds__(kMaxThreads, 1) fem_frame_kernel(FemArgs A) {
         float vin[6];
 #pragma unroll
         for (int k = 0; k < 6; ++k) vin[k] = elements_from_dl ? dl[s][k] : z[s][k];
-        float g[9];
-        load_g(gS, t, g);
-        tet_scatter(R[s], g, vin, cont + 12 * t);
+        tet_scatter(R[s], gS + 9 * t, vin, cont + 13 * t);
       }
     }
     for (int d = tid; d < ND; d += nthr) {
       const float vd = elements_from_dl ? ddl[d] : dz[d];
-      float* c = cont + 12 * NT + 7 * d;
+      float* c = cont + 13 * NT + 7 * d;
       const float nx = dn[3 * d] * vd, ny = dn[3 * d + 1] * vd, nz = dn[3 * d + 2] * vd;
       c[0] = -nx; c[1] = -ny; c[2] = -nz;
       c[3] = nx; c[4] = ny; c[5] = nz;
@@ -364,14 +349,14 @@ __global__ void __launch_bounds__(kMaxThreads, 1) fem_frame_kernel(FemArgs A) {
       sz += __shfl_xor_sync(0xffffffffu, sz, 1);
       if (i < P && (tid & 1) == 0) {
         const float w = wn[i];
-        reinterpret_cast<float4*>(uu)[i] = make_float4(w * sx, w * sy, w * sz, 0.f);
+        uu[3 * i] = w * sx; uu[3 * i + 1] = w * sy; uu[3 * i + 2] = w * sz;
       }
     } else {
       for (int i = tid; i < P; i += nthr) {
         float sx = 0.f, sy = 0.f, sz = 0.f;
         slot_sum(cont, csr, coff[i], coff[i + 1], sx, sy, sz);
         const float w = wn[i];
-        reinterpret_cast<float4*>(uu)[i] = make_float4(w * sx, w * sy, w * sz, 0.f);
+        uu[3 * i] = w * sx; uu[3 * i + 1] = w * sy; uu[3 * i + 2] = w * sz;
       }
     }
     __syncthreads();
@@ -383,9 +368,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) fem_frame_kernel(FemArgs A) {
       const int t = tid + s * nthr;
       if (t < NT) {
         float y[6], cz[6];
-        float g[9];
-        load_g(gS, t, g);
-        tet_rows(R[s], g, reinterpret_cast<const float4*>(uu), reinterpret_cast<const ushort4*>(tetS)[t], y);
+        tet_rows(R[s], gS + 9 * t, uu, reinterpret_cast<const ushort4*>(tetS)[t], y);
         compliance(nu, z[s], cz);
         const float sc = 1.f / (volS[t] * Y * h2);
 #pragma unroll
@@ -396,8 +379,8 @@ __global__ void __launch_bounds__(kMaxThreads, 1) fem_frame_kernel(FemArgs A) {
       float y = 0.f;
       if (actS[d]) {
         const int i = rowS[2 * d], j = rowS[2 * d + 1];
-        y = dn[3 * d] * (uu[4 * j] - uu[4 * i]) + dn[3 * d + 1] * (uu[4 * j + 1] - uu[4 * i + 1]) +
-            dn[3 * d + 2] * (uu[4 * j + 2] - uu[4 * i + 2]) + dat[d] * dz[d];
+        y = dn[3 * d] * (uu[3 * j] - uu[3 * i]) + dn[3 * d + 1] * (uu[3 * j + 1] - uu[3 * i + 1]) +
+            dn[3 * d + 2] * (uu[3 * j + 2] - uu[3 * i + 2]) + dat[d] * dz[d];
       }
       daz[d] = y;
     }
@@ -448,8 +431,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) fem_frame_kernel(FemArgs A) {
         if (t < NT) {
           const ushort4 id4 = reinterpret_cast<const ushort4*>(tetS)[t];  // one 8-byte load
           const int id[4] = {id4.x, id4.y, id4.z, id4.w};
-          float g[9];
-          load_g(gS, t, g);
+          const float* g = gS + 9 * t;
           const float x0 = xx[3 * id[0]], y0 = xx[3 * id[0] + 1], z0 = xx[3 * id[0] + 2];
           float F[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll
@@ -605,10 +587,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) fem_frame_kernel(FemArgs A) {
       }
       for (int d = tid; d < ND; d += nthr) dlam[d] += ddl[d];
       product(true);  // (as above: the last reduction's barrier separates the reads of uu)
-      for (int i = tid; i < P; i += nthr) {
-        const float4 u = reinterpret_cast<const float4*>(uu)[i];
-        xx[3 * i] += u.x; xx[3 * i + 1] += u.y; xx[3 * i + 2] += u.z;
-      }
+      for (int i = tid; i < P * 3; i += nthr) xx[i] += uu[i];
       __syncthreads();
     }
     // ---- velocities
@@ -665,8 +644,8 @@ __global__ void fem_node_volume_kernel(const double* X, const int* tets, const u
   double s = 0.0;
   for (int e = coff[i]; e < coff[i + 1]; ++e) {
     const int off = csr[e];
-    if (off >= 12 * NT) continue;  // a distance row's end
-    const int* id = tets + 4 * (off / 12);
+    if (off >= 13 * NT) continue;  // a distance row's end
+    const int* id = tets + 4 * (off / 13);
     double D[9];
     for (int a = 0; a < 3; ++a)
       for (int k = 0; k < 3; ++k) D[3 * k + a] = X[3 * id[a + 1] + k] - X[3 * id[0] + k];
@@ -768,8 +747,8 @@ SimStatus fem_create(const FemConfig* cfg, const FemMesh* mesh, int n_links, con
                                    "amplitude >= 0)");
   }
   // contribution slots of each particle in ascending slot order (element e vertex a: slot
-  // 4 e + a, offset 12 e + 9 for a = 0 and 12 e + 3 (a - 1) otherwise; distance row d end
-  // k: slot 4 NT + 2 d + k, offset 12 NT + 7 d + 3 k), stored as offsets of component 0
+  // 4 e + a, offset 13 e + 3 a; distance row d end k: slot 4 NT + 2 d + k, offset
+  // 13 NT + 7 d + 3 k), stored as offsets of component 0
   const int nnz = 4 * NT + 2 * ND;
   std::vector<int> cnt(P + 1, 0);
   for (int t = 0; t < NT; ++t)
@@ -780,9 +759,9 @@ SimStatus fem_create(const FemConfig* cfg, const FemMesh* mesh, int n_links, con
   for (int i = 0; i <= P; ++i) coff[i] = (unsigned short)cnt[i];
   std::vector<int> pos(cnt.begin(), cnt.end() - 1);
   for (int t = 0; t < NT; ++t)
-    for (int a = 0; a < 4; ++a) csr[pos[mesh->tets[4 * t + a]]++] = (unsigned short)(12 * t + (a == 0 ? 9 : 3 * (a - 1)));
+    for (int a = 0; a < 4; ++a) csr[pos[mesh->tets[4 * t + a]]++] = (unsigned short)(13 * t + 3 * a);
   for (int d = 0; d < ND; ++d)
-    for (int k = 0; k < 2; ++k) csr[pos[mesh->rows[2 * d + k]]++] = (unsigned short)(12 * NT + 7 * d + 3 * k);
+    for (int k = 0; k < 2; ++k) csr[pos[mesh->rows[2 * d + k]]++] = (unsigned short)(13 * NT + 7 * d + 3 * k);
   // launch shape and shared memory
   const int nthr = ((NT + kTPT - 1) / kTPT + 31) / 32 * 32;
   const FemLayout lay(P, NT, ND, nnz);
