@@ -37,7 +37,7 @@ SKIP = 0.5  # learned warm start: lambda0 = SKIP lambda_prev + m g h^2 network(f
 # transcendental counts as one operation).
 FLOP_PER_NODE_PASS = 216
 # DRAM bytes per row of the network kernel: ncu (80.80 MB read + 2.06 MB written) over a
-# 1,261,356-row launch of this build of mlp_infer_kernel
+# 1,261,356-row launch of the current mlp_infer_kernel
 MLP_DRAM_BYTES_PER_ROW = (80.799232e6 + 2.060544e6) / 1261356
 # DRAM bytes per node of a split-mode launch of the 32-lane x 3-node solver kernel: ncu
 # (8.27776 MB read + 0.06784 MB written) over the 93,177 nodes that layout owns in the
