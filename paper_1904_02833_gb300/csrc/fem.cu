@@ -51,7 +51,7 @@ struct FemLayout {
   // floats (per-element and per-row records padded to an odd number of words: 13 per
   // element's contribution slots, 7 per element's multipliers / inverse diagonals, 7 per
   // distance row's slots, so that consecutive threads hit distinct banks)
-  int g, vol, lam, idg, cont, xs, xx, vv, uu, wn, dn, drest, dat, did, dlam, ddl, dz, dp, dq, daz, red, n_float;
+  int g, scl, lam, idg, cont, xs, xx, vv, uu, wn, dn, drest, dat, did, dlam, ddl, dz, dp, dq, daz, red, n_float;
   // unsigned shorts (after the floats)
   int tet, row, coff, csr, n_short;
   // bytes (after the shorts)
@@ -60,7 +60,7 @@ struct FemLayout {
   __host__ __device__ FemLayout(int P, int NT, int ND, int nnz) {
     int o = 0;
     g = o; o += NT * 9;
-    vol = o; o += NT;
+    scl = o; o += NT;  // compliance scale 1 / (V Y h^2) per element
     lam = o; o += NT * 7;
     idg = o; o += NT * 7;
     cont = o; o += 13 * NT + 7 * ND;  // element e vertex a comp k at 13 e + 3 a + k; row d end k at 13 NT + 7 d + 3 k
@@ -276,7 +276,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) fem_frame_kernel(FemArgs A) {
   float* fs = reinterpret_cast<float*>(smem_raw);
   unsigned short* us = reinterpret_cast<unsigned short*>(fs + L.n_float);
   unsigned char* ub = reinterpret_cast<unsigned char*>(us + L.n_short);
-  float *gS = fs + L.g, *volS = fs + L.vol, *lamT = fs + L.lam, *idT = fs + L.idg, *cont = fs + L.cont;
+  float *gS = fs + L.g, *scS = fs + L.scl, *lamT = fs + L.lam, *idT = fs + L.idg, *cont = fs + L.cont;
   float *xs = fs + L.xs, *xx = fs + L.xx, *vv = fs + L.vv, *uu = fs + L.uu, *wn = fs + L.wn;
   float *dn = fs + L.dn, *drest = fs + L.drest, *dat = fs + L.dat, *did = fs + L.did, *dlam = fs + L.dlam;
   float *ddl = fs + L.ddl, *dz = fs + L.dz, *dp = fs + L.dp, *dq = fs + L.dq, *daz = fs + L.daz, *red = fs + L.red;
@@ -288,10 +288,13 @@ __global__ void __launch_bounds__(kMaxThreads, 1) fem_frame_kernel(FemArgs A) {
   const int P = A.P, NT = A.NT, ND = A.ND;
   const FemLinkParams pr = A.prm[link];
   const float Y = pr.youngs, nu = pr.poisson;
+  const float h = (float)(A.dt / A.n_sub);
+  const float h2 = h * h;
 
-  // ---- mesh and state of this link into shared memory
+  // ---- mesh and state of this link into shared memory; per element the compliance
+  // scale 1 / (V Y h^2) of its rows (E / h^2 = scale x C)
   for (int i = tid; i < NT * 9; i += nthr) gS[i] = A.g[i];
-  for (int i = tid; i < NT; i += nthr) volS[i] = A.vol[i];
+  for (int i = tid; i < NT; i += nthr) scS[i] = 1.f / (A.vol[i] * Y * h2);
   for (int i = tid; i < NT * 4; i += nthr) tetS[i] = A.tet[i];
   for (int i = tid; i < ND * 2; i += nthr) rowS[i] = A.row[i];
   for (int i = tid; i < ND; i += nthr) kindS[i] = A.kind[i];
@@ -303,8 +306,6 @@ __global__ void __launch_bounds__(kMaxThreads, 1) fem_frame_kernel(FemArgs A) {
   for (int i = tid; i < P; i += nthr) wn[i] = A.fixed[i] ? 0.f : 1.f / (pr.density * A.vnode[i]);
   __syncthreads();
 
-  const float h = (float)(A.dt / A.n_sub);
-  const float h2 = h * h;
   const float damp = expf(-pr.damping * h);
   float r_frame = 0.f;
   int mv_frame = 0;
@@ -370,7 +371,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) fem_frame_kernel(FemArgs A) {
         float y[6], cz[6];
         tet_rows(R[s], gS + 9 * t, uu, reinterpret_cast<const ushort4*>(tetS)[t], y);
         compliance(nu, z[s], cz);
-        const float sc = 1.f / (volS[t] * Y * h2);
+        const float sc = scS[t];
 #pragma unroll
         for (int k = 0; k < 6; ++k) az[s][k] = y[k] + sc * cz[k];
       }
@@ -456,7 +457,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) fem_frame_kernel(FemArgs A) {
 #pragma unroll
           for (int k = 0; k < 6; ++k) lam6[k] = lamT[7 * t + k];
           compliance(nu, lam6, al);
-          const float sc = 1.f / (volS[t] * Y * h2);
+          const float sc = scS[t];
           // diagonal: sum_a w_a |Sigma_k g_a|^2 + sc C_kk
           const float w0 = wn[id[0]];
           float g0x = 0.f, g0y = 0.f, g0z = 0.f;
