@@ -199,6 +199,64 @@ def test_curvature_is_linear_in_small_pressures():
     assert tip[0] > 0 and tip[1] / tip[0] == pytest.approx(2.0, rel=1e-2)
 
 
+def test_newton_step_equals_dense_schur_solve():
+    """Sec. IV-D: one Newton step whose PCR iterations run to convergence moves the
+    particles by M^-1 J^T dlambda with (J M^-1 J^T + E / h^2) dlambda = -c, assembled here
+    densely from the element rows (the paper's compliance block per element) and the
+    centre-layer, perimeter and driven-chamber distance rows at the predicted positions."""
+    M = _small_mesh(rows=True)
+    X, T, fixed = M["X"], M["tets"], M["fixed"]
+    p, dt, g = 3000.0, 1.0 / 60.0, np.array([0.0, -1.0, -9.81])
+    w = W.fem_const_pressure(1, [p], poisson=0.45, alpha_inext=1e-5, alpha_perim=2e-5)
+    K = 3000
+    s = W.fem_settings(dt=dt, n_sub=1, iters=1 + K, tol=0.0, pcr_iters=K, gravity=g)
+    o = F.OracleFem(M, w, s, n_threads=1)
+    o.step(1)
+    assert o.mv[0] == 1 + K
+    P, h = len(X), dt
+    Y, nu = w["youngs"][0], w["poisson"][0]
+    m = _lumped_masses(M, w["density"][0])
+    Wm = np.where(fixed == 1, 0.0, 1.0 / m)
+    xt = X + np.where(fixed[:, None] == 1, 0.0, h * h * g[None, :])
+    C = np.zeros((6, 6))
+    C[:3, :3] = -nu
+    np.fill_diagonal(C[:3, :3], 1.0)
+    C[3:, 3:] = np.eye(3) * (1.0 + nu)
+    J, c, comp = [], [], []
+    for t in T:
+        ct, G, _, vol = F.tet(X[t], xt[t])
+        for k in range(6):
+            row = np.zeros(3 * P)
+            for a in range(4):
+                row[3 * t[a]:3 * t[a] + 3] = G[k, a]
+            J.append(row)
+            c.append(ct[k])
+        comp.append(C / (vol * Y * h * h))
+    eps = 1.0 + abs(p) / Y
+    for (i, j), kind in zip(M["rows"], M["kinds"]):
+        if kind == W.FEM_ACT_LEFT or Wm[i] + Wm[j] == 0.0:
+            continue  # the left chamber is not driven; rows between held particles do not exist
+        r0 = np.linalg.norm(X[j] - X[i])
+        e = xt[j] - xt[i]
+        n = e / np.linalg.norm(e)
+        row = np.zeros(3 * P)
+        row[3 * j:3 * j + 3], row[3 * i:3 * i + 3] = n, -n
+        J.append(row)
+        c.append(np.linalg.norm(e) - (r0 * eps if kind == W.FEM_ACT_RIGHT else r0))
+        alpha = {W.FEM_INEXT: w["alpha_inext"][0], W.FEM_PERIM: w["alpha_perim"][0]}.get(kind, w["alpha_act"][0])
+        comp.append(np.array([[alpha / (h * h)]]))
+    J, c = np.array(J), np.array(c)
+    E = np.zeros((len(c), len(c)))
+    o_ = 0
+    for B in comp:
+        E[o_:o_ + len(B), o_:o_ + len(B)] = B
+        o_ += len(B)
+    Wv = np.repeat(Wm, 3)
+    dl = np.linalg.solve((J * Wv) @ J.T + E, -c)
+    want = xt + (Wv * (J.T @ dl)).reshape(-1, 3)
+    assert np.abs(o.x[0] - want).max() < 1e-9 * np.abs(want - xt).max()
+
+
 def test_actuation_row_rest_length_follows_eq2():
     """One element, three vertices held, a hard actuation row from a held vertex to the
     free one: after a solved substep their distance is r (1 + |p| / Y) when that row's
