@@ -83,11 +83,12 @@ def test_compliant_rows_and_clamped_command():
 
 def test_largest_block_and_a_mesh_without_distance_rows():
     """15 cross-sections (1008 elements, 512 threads per block, 205 KB of shared memory,
-    the largest launch shape) and the 13-section mesh with no distance rows at all."""
+    the largest launch shape) and the 13-section mesh with no distance rows at all,
+    sagging under gravity."""
     M = W.fem_link_mesh(m=8, n_sec=15)
     _check(M, W.fem_links(4, seed=16), W.fem_settings())
     M0 = dict(W.fem_link_mesh(), rows=np.zeros((0, 2), np.int32), kinds=np.zeros(0, np.int32))
-    _check(M0, W.fem_links(3, seed=17), W.fem_settings())
+    _check(M0, W.fem_links(3, seed=17), W.fem_settings(gravity=(0.0, 0.0, -9.81)), frames=2)
 
 
 def test_tolerance_stops_the_newton_loop():
