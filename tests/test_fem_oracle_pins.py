@@ -2,8 +2,6 @@
 mathematics: scipy's polar decomposition, strains of known deformations, central
 differences, the textbook linear FEM stiffness assembled here from shape functions,
 momentum conservation and the actuation rest length of Eq. 2."""
-import math
-
 import numpy as np
 import pytest
 
