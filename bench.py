@@ -569,9 +569,17 @@ def cpu_baseline(w, s, n_sample=None, budget_s=20.0):
         if time.perf_counter() - t0 > budget_s / 2 or steps >= 8:
             break
     dt = time.perf_counter() - t0
+    # the same oracle on one host core, on a smaller sample of the same snakes
+    n1 = max(1, min(4, n_sample))
+    o1 = oracle.OracleSim(W.subset(w, sel[:n1]), s, n_threads=1)
+    t1 = time.perf_counter()
+    o1.step(1)
+    dt1 = time.perf_counter() - t1
     return {"value": n_sample * steps / dt, "unit": "env-steps/s", "cores": cores, "kind": "oracle",
             "sample": "%d snakes drawn from the batch x %d env-steps (FP64, OpenMP over snakes), "
-                      "%.1f s" % (n_sample, steps, dt)}
+                      "%.1f s" % (n_sample, steps, dt),
+            "single_thread": {"value": n1 / dt1, "unit": "env-steps/s", "cores": 1,
+                              "sample": "%d of those snakes x 1 env-step, %.1f s" % (n1, dt1)}}
 
 
 def workload_config(total_nodes, world):

@@ -23,3 +23,13 @@ def test_reference_arm_prints_one_contract_line():
     assert d["metric"].startswith("snake env-steps/s")
     assert d["config"]["snakes_per_gpu"] == 16384 and d["config"]["nodes_per_gpu"] > 16384 * 20
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_cpu_baseline_reports_all_cores_and_one_core():
+    sys.path.insert(0, ROOT)
+    import bench
+    import workloads as W
+    w = W.learned(n=64, seed=4)
+    r = bench.cpu_baseline(w, W.solver_settings(iters=bench.CAP, tol=bench.TOL), n_sample=4, budget_s=1.0)
+    assert r["kind"] == "oracle" and r["value"] > 0 and r["cores"] >= 1
+    assert r["single_thread"]["cores"] == 1 and r["single_thread"]["value"] > 0
