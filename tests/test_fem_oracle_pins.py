@@ -255,6 +255,32 @@ def test_newton_step_equals_dense_schur_solve():
     assert np.abs(o.x[0] - want).max() < 1e-9 * np.abs(want - xt).max()
 
 
+@pytest.mark.parametrize("p", [4000.0, 0.0])
+def test_residual_is_the_largest_normalised_row_value(p):
+    """With no solve (a cap of 0 products) the reported residual is the largest row value
+    at the predicted positions with zero multipliers: strains as they are, distance rows
+    |length - rest| over their unactuated rest length, the driven chamber's rows at rest
+    length r (1 + |p| / Y), the other chamber's rows and rows between held particles absent."""
+    M = _small_mesh(rows=True)
+    X, fixed = M["X"], M["fixed"]
+    rng = np.random.default_rng(6)
+    w = W.fem_const_pressure(1, [p])
+    o = F.OracleFem(M, w, W.fem_settings(n_sub=1, iters=0), n_threads=1)
+    x0 = X + np.where(fixed[:, None] == 1, 0.0, rng.normal(size=X.shape) * 2e-4)
+    o.x[0] = x0
+    o.step(1)
+    assert o.mv[0] == 0 and np.array_equal(o.x[0], x0)
+    want = max(np.abs(F.tet(X[t], x0[t])[0]).max() for t in M["tets"])
+    eps = 1.0 + p / w["youngs"][0]
+    for (i, j), kind in zip(M["rows"], M["kinds"]):
+        if kind == W.FEM_ACT_LEFT or (kind == W.FEM_ACT_RIGHT and p == 0) or (fixed[i] and fixed[j]):
+            continue
+        r0 = np.linalg.norm(X[j] - X[i])
+        rest = r0 * eps if kind == W.FEM_ACT_RIGHT else r0
+        want = max(want, abs(np.linalg.norm(x0[j] - x0[i]) - rest) / r0)
+    assert o.resid[0] == pytest.approx(want, rel=1e-12)
+
+
 def test_actuation_row_rest_length_follows_eq2():
     """One element, three vertices held, a hard actuation row from a held vertex to the
     free one: after a solved substep their distance is r (1 + |p| / Y) when that row's
