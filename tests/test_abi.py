@@ -107,3 +107,19 @@ def test_product_path_has_no_oracle_dependency():
             if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "oracle" not in txt.lower(), os.path.join(dirpath, f)
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """No fallback: without the built library every entry point of the binding raises."""
+    from paper_1904_02833_gb300 import _native
+    monkeypatch.setattr(_native, "LIB_PATH", str(tmp_path / "libsnakesim.so"))
+    monkeypatch.setattr(_native, "_lib", None)
+    with pytest.raises(ImportError, match="not built"):
+        _native.load()
+    import workloads as W
+    from paper_1904_02833_gb300.fem import FemSim
+    from paper_1904_02833_gb300.sim import SnakeSim
+    with pytest.raises(ImportError):
+        FemSim(W.fem_link_mesh(m=4, n_sec=2), W.fem_links(1), W.fem_settings(), device="cpu")
+    with pytest.raises(ImportError):
+        SnakeSim(W.single_snake(), W.solver_settings())
