@@ -281,6 +281,31 @@ def test_residual_is_the_largest_normalised_row_value(p):
     assert o.resid[0] == pytest.approx(want, rel=1e-12)
 
 
+def test_whole_step_is_rotation_equivariant():
+    """Every row is invariant under rotations (corotational strains, distances), so a
+    frame started from Q x with gravity Q g ends at Q times the frame started from x with
+    gravity g, through the unconverged fixed-budget Newton + PCR solve as well."""
+    M = _small_mesh(rows=True)
+    X, fixed = M["X"], M["fixed"]
+    rng = np.random.default_rng(7)
+    Q = _rot(rng)
+    g = np.array([0.3, -0.5, -9.81])
+    x0 = X + np.where(fixed[:, None] == 1, 0.0, rng.normal(size=X.shape) * 1e-4)
+    v0 = np.where(fixed[:, None] == 1, 0.0, rng.normal(size=X.shape) * 1e-2)
+    w = W.fem_const_pressure(1, [3000.0], poisson=0.45, alpha_inext=1e-5)
+    out = []
+    for R, gg in ((np.eye(3), g), (Q, Q @ g)):
+        o = F.OracleFem(M, w, W.fem_settings(gravity=tuple(gg)), n_threads=1)
+        o.x[0] = x0 @ R.T
+        o.v[0] = v0 @ R.T
+        o.step(2)
+        out.append((o.x[0].copy(), o.v[0].copy(), o.resid[0]))
+    (x1, v1, r1), (x2, v2, r2) = out
+    assert np.abs(x2 - x1 @ Q.T).max() < 1e-12
+    assert np.abs(v2 - v1 @ Q.T).max() < 1e-7 * np.abs(v1).max()  # (x rounding / h)
+    assert r2 == pytest.approx(r1, rel=1e-8)
+
+
 def test_actuation_row_rest_length_follows_eq2():
     """One element, three vertices held, a hard actuation row from a held vertex to the
     free one: after a solved substep their distance is r (1 + |p| / Y) when that row's
