@@ -520,3 +520,28 @@ def test_calibration_gradient_matches_central_differences():
                 lp.append(np.mean(np.sum((tp[:, sgn_snake] - target[:, sgn_snake]) ** 2, -1)))
             fd = (lp[0] - lp[1]) / (2 * hstep)
             assert grad[sgn_snake, j] == pytest.approx(fd, rel=2e-3, abs=1e-9 * abs(loss[sgn_snake]) / hstep), (nm, sgn_snake)
+
+
+@pytest.mark.parametrize("mu_side", [0.0, 0.9])
+def test_env_steps_are_equivariant_under_rotations_about_the_vertical(mu_side):
+    """Every row is invariant under rotations about z (stretch, heading difference,
+    elevation, contact height) and the friction pair is limited by a disc, or an ellipse
+    in the body frame, so two snakes that differ only by their initial heading evolve
+    into each other rotated, through unconverged fixed-count Jacobi passes as well."""
+    w = W.batched(n=2, seed=21, links=(3, 3))
+    for k in W.FLOAT_FIELDS:
+        w[k][1] = w[k][0]
+    theta = 1.1
+    w["yaw0"][:] = [0.4, 0.4 + theta]
+    w["x0"][:] = 0.0
+    w["y0"][:] = 0.0
+    w["mu_side"][:] = mu_side
+    o = oracle.OracleSim(w, W.solver_settings(iters=10))
+    o.step(3)
+    c, s_ = math.cos(theta), math.sin(theta)
+    Rz = np.array([[c, -s_, 0.0], [s_, c, 0.0], [0.0, 0.0, 1.0]])
+    a, b = o.x[o.snake_nodes(0)], o.x[o.snake_nodes(1)]
+    assert np.abs(b - a @ Rz.T).max() < 1e-12
+    va, vb = o.v[o.snake_nodes(0)], o.v[o.snake_nodes(1)]
+    assert np.abs(vb - va @ Rz.T).max() < 1e-9 * np.abs(va).max()
+    assert np.abs(va).max() > 1e-3  # the snakes are moving
