@@ -8,9 +8,10 @@ loops, FP64, templated on a dual-number type for parameter derivatives) and
 ``fem_oracle.cpp`` (wrapped by ``fem.py``).
 
 Parity unpinned: the full locomotion runs (one 4-link snake, batched snakes) have no
-closed form and no published trajectory data; they are checked only against this
-oracle.  Everything the oracle computes on the way is pinned by the tests listed in
-``snake_oracle.cpp``.
+closed form and no published trajectory data; only their invariances (momentum, rotation
+about the vertical) are pinned, and the GPU path is checked against this oracle.
+Everything the oracle computes on the way is pinned by the tests listed in
+``snake_oracle.cpp`` and ``fem_oracle.cpp``.
 """
 from __future__ import annotations
 

@@ -27,7 +27,9 @@
 // Parity pins (see tests/test_oracle_*.py): discrete circular arc under uniform
 // pressure, small-deflection cantilever sag, pendulum period, momentum conservation,
 // brute-force Newton on a 3-node chain, finite-difference constraint gradients,
-// closed-form latency-filter step response, hand-computed gait values.
+// closed-form latency-filter step response, hand-computed gait and chamber-law values,
+// Coulomb sliding distances (isotropic and anisotropic), a dense Schur solve for the
+// Newton + PCR step, and equivariance of whole env-steps under rotations about z.
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
