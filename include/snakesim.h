@@ -20,7 +20,9 @@
  *       (Eq. 7) and Coulomb friction rows, in parallel, with compliance alpha / h^2,
  *   a6  measures the normalised residual and stops at the tolerance or the cap,
  *   a7  updates velocities from the displacement with exponential damping.
- * Thousands of snakes of uneven length run in one persistent kernel.
+ * Thousands of snakes of uneven length run together: the snakes are grouped by length
+ * into lane layouts (8, 16 or 32 lanes per snake, 1-4 nodes per lane), and each layout
+ * runs one persistent kernel that takes its snakes from a device-side work queue.
  *
  * Conventions (every call):
  *   - Every call returns a SimStatus; nothing aborts or throws across the ABI.  The text
