@@ -52,6 +52,8 @@ def lib():
         L.oracle_step.argtypes = [ctypes.c_int, P, P, P, P, P, ctypes.c_longlong, ctypes.c_int,
                                   P, P, P, P, P, P, P, P, P, ctypes.c_int]
         L.oracle_rows.argtypes = [ctypes.c_int, ctypes.c_int, P, P, P, P, P, P, P, P]
+        L.oracle_residual.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, P, P, P, P, P, P]
+        L.oracle_residual.restype = ctypes.c_double
         L.oracle_calib_grad.argtypes = [ctypes.c_int, P, P, P, P, P, ctypes.c_longlong,
                                         ctypes.c_int, P, P, P, P, P, P, P, ctypes.c_int]
         L.oracle_features.argtypes = [ctypes.c_int, P, P, P, P, P, ctypes.c_longlong, P, P, P, P,
@@ -181,3 +183,13 @@ def rows(w1: dict, settings: dict, x, xs, press):
     lib().oracle_rows(int(w1["n_links"][0]), int(w1["seg_per_link"][0]), _p(prm), _p(cfg),
                       _p(x), _p(xs), _p(press), _p(c), _p(g), _p(on))
     return c, g, on.astype(bool)
+
+
+def residual(w1: dict, settings: dict, x, xs, press, lam) -> float:
+    """The normalised residual the solver loops stop on, for one snake (index 0 of w1)
+    at positions x, substep-start positions xs, pressures press and multipliers lam."""
+    prm = pack_params(w1)[:1]
+    cfg = pack_cfg(settings)
+    arr = [np.ascontiguousarray(a, np.float64) for a in (x, xs, press, lam)]
+    return float(lib().oracle_residual(int(w1["n_links"][0]), int(w1["seg_per_link"][0]),
+                                       int(w1["n_fixed"][0]), _p(prm), _p(cfg), *map(_p, arr)))

@@ -29,7 +29,10 @@
 // brute-force Newton on a 3-node chain, finite-difference constraint gradients,
 // closed-form latency-filter step response, hand-computed gait and chamber-law values,
 // Coulomb sliding distances (isotropic and anisotropic), a dense Schur solve for the
-// Newton + PCR step, and equivariance of whole env-steps under rotations about z.
+// Newton + PCR step, equivariance of whole env-steps under rotations about z, and the
+// normalised residual on hand-built states whose value the definitions fix (every
+// term: bilateral rows, the Fischer-Burmeister contact value, sticking and sliding
+// friction pairs, rows on fixed nodes).
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
@@ -868,6 +871,28 @@ int oracle_rows(int nl, int seg, const double* prm1, const double* cfg, const do
   for (int i = 0; i < S.N * NK; ++i) { c[i] = R.c[i]; on[i] = R.on[i]; }
   for (int i = 0; i < S.N * NK * 3; ++i) { g[3 * i] = R.g[i].x; g[3 * i + 1] = R.g[i].y; g[3 * i + 2] = R.g[i].z; }
   return 0;
+}
+
+// The normalised residual residual() reports for one snake (n_fixed leading nodes held)
+// at positions x, substep-start positions xs, chamber pressures press and multipliers
+// lam[N][6]: the value the Jacobi and Newton loops compare against the tolerance.
+double oracle_residual(int nl, int seg, int nfix, const double* prm1, const double* cfg,
+                       const double* x, const double* xs, const double* press, const double* lam) {
+  int one_nl = nl, one_seg = seg, one_fix = nfix;
+  Snake<double> S = load_snake<double>(&one_nl, &one_seg, &one_fix, prm1, 0);
+  Cfg C = load_cfg(cfg);
+  std::vector<V3<double>> X(S.N), XS(S.N);
+  for (int i = 0; i < S.N; ++i) { X[i] = {x[3 * i], x[3 * i + 1], x[3 * i + 2]}; XS[i] = {xs[3 * i], xs[3 * i + 1], xs[3 * i + 2]}; }
+  std::vector<double> theta(S.N, 0.0), w(S.N), L(lam, lam + (size_t)S.N * NK);
+  for (int i = 1; i <= S.N - 2; ++i) {
+    if (i % S.seg == 0) continue;
+    int k = i / S.seg;
+    theta[i] = S.gain * (press[2 * k] - press[2 * k + 1]) * S.L0;
+  }
+  for (int i = 0; i < S.N; ++i) w[i] = (i < S.nfix) ? 0.0 : 1.0 / S.mass;
+  Rows<double> R; R.init(S.N);
+  eval_rows(S, C, X, XS, theta, R);
+  return residual(S, C, R, w, L, XS);
 }
 
 // Forward-mode gradient of the calibration loss
