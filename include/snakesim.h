@@ -205,9 +205,10 @@ SimStatus sim_set_layout(SimHandle* h, int nodes, int lanes, int nodes_per_lane)
 SimStatus sim_step_graph(SimHandle* h, int n_steps);
 
 /* Saves / restores the whole simulation state (positions, velocities, pressures,
- * multipliers, env-step counter, substep position of split stepping) in a
- * library-owned snapshot; stream-ordered.  Restoring without a saved snapshot is
- * SIM_EINVAL. */
+ * multipliers, per-snake residual, update count and status, env-step counter, substep
+ * position of split stepping and, inside a split env-step, the begun substep's
+ * features) in a library-owned snapshot; stream-ordered.  Restoring without a saved
+ * snapshot is SIM_EINVAL. */
 SimStatus sim_snapshot_save(SimHandle* h);
 SimStatus sim_snapshot_restore(SimHandle* h);
 
@@ -249,6 +250,19 @@ SimStatus sim_kernel_times(SimHandle* h, float* ms, int64_t* launches);
 /* Frees the handle and its device buffers (synchronises the stream).  NULL is ok. */
 SimStatus sim_destroy(SimHandle* h);
 
+/* Splits a batch for several GPUs: the snakes are independent (each one's substeps touch
+ * only its own nodes, Sec. IV), so one batch runs as contiguous snake ranges, one handle
+ * per range and GPU, with no exchange between them.  params: host [n_snakes];
+ * first: host int32 [parts + 1], receives the ranges: part p owns snakes
+ * [first[p], first[p + 1]), first[0] = 0, first[parts] = n_snakes.  The ranges are
+ * balanced by node count (n_links * seg_per_link + 1 per snake): boundary p is the snake
+ * boundary whose node prefix sum is nearest to p / parts of the total (the lower one on
+ * a tie), kept non-decreasing, so every part holds the ideal share to within the nodes of
+ * one snake (parts beyond the number of snakes may be empty).  Host computation only (no
+ * CUDA call, no GPU needed).  Errors: SIM_EINVAL (n_snakes < 1, parts < 1, null
+ * pointers, a snake with n_links or seg_per_link < 1). */
+SimStatus sim_partition(int n_snakes, const SnakeParams* params, int parts, int32_t* first);
+
 /* Measures the FP32 arithmetic roof the solvers are compared against: enqueues on
  * `stream` n_blocks blocks of 256 threads, each thread running `iters` rounds of 16 x 8
  * independent fused multiply-adds (256 FLOP per round and thread), and writes one
@@ -275,8 +289,10 @@ SimStatus mlp_create(void* stream, MlpHandle** out);
 /* Sets / reads the FP32 parameter vector; setting also resets the Adam moments. */
 SimStatus mlp_set_params(MlpHandle* m, const float* params, int is_device);
 SimStatus mlp_get_params(MlpHandle* m, float* params, int is_device);
-/* out[r] for feat [rows][32] bf16 (device pointers).  Synchronises the stream;
- * SIM_ECUDA if a tensor-core wait timed out. */
+/* out[r] for feat [rows][32] bf16 (device pointers, feat 16-byte aligned).
+ * Synchronises the stream; SIM_EINVAL for a misaligned feat, SIM_ECUDA if a tensor-core
+ * wait timed out.  The training calls below take feat with the same layout and
+ * alignment. */
 SimStatus mlp_forward(MlpHandle* m, const void* feat, int64_t rows, float* out);
 /* Gradient of L = scale * sum_r (y_r - target_r)^2 into grad[MLP_NUM_PARAMS] and L into
  * *loss (device pointers, either may be NULL).  Synchronises the stream. */
@@ -296,16 +312,18 @@ SimStatus mlp_destroy(MlpHandle* m);
  * library none).  No counterpart in the paper.
  * params: device FP32 parameter vector of n_params = MLP_NUM_PARAMS values (layout as
  * above, owned by the caller); feat: device bf16 [rows][32]; out: device FP32 [rows];
- * stream: cudaStream_t.  Calls no cudaMalloc / cudaFree: the bfloat16 weight copies and
- * the timeout flag live in a fixed file-scope device array of MLP_NOALLOC_SCRATCH_BYTES
- * bytes, held by every GPU that loads the library until the process exits.  The first
- * call on a device, with that device current, looks up the array's device address and
- * sets the kernel's shared-memory limit; make that first call before any stream capture
- * begins.  The array is shared by every call on a device and keeps the
- * last call's contents, so calls whose GPU work overlaps (other streams, other threads)
- * race; order them on one stream.  Synchronises `stream`.  Errors: SIM_EINVAL (null
- * pointers, rows < 0, n_params other than MLP_NUM_PARAMS -- the array holds exactly one
- * network's weights), SIM_ECUDA. */
+ * stream: cudaStream_t; feat must be 16-byte aligned.  Calls no cudaMalloc / cudaFree:
+ * the bfloat16 weight copies and the timeout flag live in a fixed file-scope device array
+ * of MLP_NOALLOC_SCRATCH_BYTES bytes, held by every GPU that loads the library until the
+ * process exits.  The first call on a device, with that device current, looks up the
+ * array's device address and sets the kernel's shared-memory limit; make that first
+ * call before any stream capture begins.  The set-up is keyed on the device's current
+ * context, so the first call after a cudaDeviceReset repeats it.  The array is shared by
+ * every call on a device and keeps the last call's contents (the call clears the flag it
+ * needs at zero), so calls whose GPU work overlaps (other streams, other threads) race;
+ * order them on one stream.  Synchronises `stream`.  Errors: SIM_EINVAL (null pointers,
+ * rows < 0, a misaligned feat, n_params other than MLP_NUM_PARAMS -- the array holds
+ * exactly one network's weights), SIM_ECUDA. */
 #define MLP_NOALLOC_SCRATCH_BYTES 41216
 SimStatus mlp_forward_noalloc(const float* params, int32_t n_params, const void* feat,
                               int64_t rows, float* out, void* stream);
@@ -330,6 +348,28 @@ SimStatus sim_split_finish(SimHandle* h);
  * starts at row first_row[s] (sim_feature_offsets, host array of n_snakes). */
 SimStatus sim_features(SimHandle* h, void** feat, int64_t* rows);
 SimStatus sim_feature_offsets(SimHandle* h, int32_t* first_row);
+
+/* Training rows of the learned warm start, for the substep in progress of split stepping
+ * (after sim_split_begin, before the sim_split_finish that completes it).  The network's
+ * output y enters the warm start as lambda0 = beta lambda_prev + m g h^2 y, so the
+ * target that makes the warm start land on a reference solution lambda_star is
+ *   y* = (lambda_star - beta lambda_prev) / (m g h^2)
+ * with m the snake's node mass, g = 9.81 m/s^2 and h = dt / n_sub of the current
+ * configuration.  For every existing row of the substep (the rows whose features carry
+ * a row kind: stretch rows of nodes 0 .. N-2, yaw and pitch rows of nodes 1 .. N-2, and
+ * with contact on the contact and two friction rows of every free node), snake by snake
+ * and node by node with the row kinds in order, the call copies the row's 32 bf16
+ * features to feat_out and writes y* to target_out.
+ * lam_star, lam_prev: device FP32 [nodes][6] in node order (the layout of
+ * sim_get_lambda; typically lambda_prev read before the substep and lambda_star after
+ * solving it to a tight tolerance from a snapshot).  feat_out: device bf16
+ * [capacity][32], 16-byte aligned; target_out: device FP32 [capacity].  *n_rows (host)
+ * receives the number of existing rows; with feat_out and target_out both NULL only
+ * the count is returned.  Asynchronous on the handle's stream.  Errors: SIM_EINVAL (no
+ * substep in progress, capacity below the row count, misaligned or missing buffers,
+ * beta outside [0, 1]), SIM_ECUDA. */
+SimStatus sim_training_rows(SimHandle* h, const float* lam_star, const float* lam_prev, float beta,
+                            void* feat_out, float* target_out, int64_t capacity, int64_t* n_rows);
 
 /* Text of the last error raised on the calling thread ("" if none). */
 const char* sim_last_error(void);

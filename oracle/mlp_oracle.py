@@ -87,3 +87,26 @@ def loss_and_grad(p, x, t, scale, bf16_ops=True):
     grad = {"W1": r(dz1).T @ xr, "b1": dz1.sum(0), "W2": dz2r.T @ h1, "b2": dz2.sum(0),
             "w3": g @ h2, "b3": np.array([g.sum()])}
     return L, pack(grad)
+
+
+def training_rows(node_off, mass, feat, lam_star, lam_prev, beta, h, g=9.81):
+    """Training rows of the learned warm start (test infrastructure).
+
+    The warm start of a substep is lambda0 = beta lambda_prev + m g h^2 y with y the
+    network's output (the oracle's snake_step), so the output that makes it land on a
+    reference solution lambda_star is y* = (lambda_star - beta lambda_prev) / (m g h^2).
+    For every row whose features carry a row kind (a one-hot entry among the first six),
+    snake by snake and node by node with the kinds in order, returns the row's features
+    and y*.  node_off: [snakes + 1]; mass: [snakes]; feat: [nodes * 6, >= 24] in node
+    order; lam_star, lam_prev: [nodes, 6]."""
+    F, T = [], []
+    for s in range(len(node_off) - 1):
+        sc = float(mass[s]) * g * h * h
+        for i in range(int(node_off[s]), int(node_off[s + 1])):
+            for k in range(6):
+                r = 6 * i + k
+                if not np.any(feat[r, :6] != 0):
+                    continue
+                F.append(feat[r])
+                T.append((float(lam_star[i, k]) - beta * float(lam_prev[i, k])) / sc)
+    return np.array(F), np.array(T)

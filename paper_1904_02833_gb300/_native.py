@@ -100,6 +100,8 @@ SIGNATURES = {
     "sim_split_begin": [H],
     "sim_split_finish": [H],
     "sim_features": [H, ctypes.POINTER(P), I64P],
+    "sim_training_rows": [H, P, P, ctypes.c_float, P, P, ctypes.c_int64, I64P],
+    "sim_partition": [ctypes.c_int, ctypes.POINTER(SnakeParams), ctypes.c_int, P],
     "mlp_create": [P, ctypes.POINTER(H)],
     "mlp_set_params": [H, P, ctypes.c_int],
     "mlp_get_params": [H, P, ctypes.c_int],

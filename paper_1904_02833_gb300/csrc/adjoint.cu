@@ -593,12 +593,30 @@ struct CalibState {
   float *rec_x = nullptr, *rec_v = nullptr, *rec_p = nullptr, *iters = nullptr;
   float *xb = nullptr, *vb = nullptr, *pb = nullptr;
   int n_ckpt = 0, n_rec = 0;
+  // allocated sizes (floats) of the buffers above, in the same order: buffers grow when a
+  // run needs more and are otherwise kept from call to call (no allocation, and no
+  // free, on the path of a repeated run)
+  size_t cap[14] = {};
+  float** slot(int i) {
+    float** ptrs[] = {&theta, &x, &v, &p, &ck_x, &ck_v, &ck_p, &rec_x, &rec_v, &rec_p, &iters, &xb, &vb, &pb};
+    return ptrs[i];
+  }
+  cudaError_t grow(int i, size_t n) {
+    if (n <= cap[i]) return cudaSuccess;
+    float** q = slot(i);
+    if (*q) cudaFree(*q);
+    *q = nullptr;
+    cap[i] = 0;
+    cudaError_t e = cudaMalloc(q, n * sizeof(float));
+    if (e == cudaSuccess) cap[i] = n;
+    return e;
+  }
   void release() {
-    float* ptrs[] = {theta, x, v, p, ck_x, ck_v, ck_p, rec_x, rec_v, rec_p, iters, xb, vb, pb};
-    for (float* q : ptrs) if (q) cudaFree(q);
+    for (int i = 0; i < 14; ++i) if (*slot(i)) cudaFree(*slot(i));
     *this = CalibState();
   }
 };
+enum { kTheta, kX, kV, kP, kCkX, kCkV, kCkP, kRecX, kRecV, kRecP, kIters, kXb, kVb, kPb };
 
 }  // namespace snakesim
 
@@ -669,20 +687,19 @@ SimStatus calib_forward(CalibState& C, const SnakeParams* prm, const int* no, co
                         int n_sub, int K, int contact, double dt, float omega, const float* gvec,
                         float4* pos4, float4* vel4, float2* press2, float* tips, cudaStream_t st,
                         std::string& err) {
-  C.release();
   C.n_snakes = n_snakes; C.n_max = n_max; C.l_max = l_max; C.n_sub = n_sub; C.K = K; C.contact = contact;
   C.ckpt = ckpt; C.n_steps = n_steps; C.step0 = step0; C.h_d = dt / n_sub; C.h = (float)C.h_d;
   C.omega = omega; C.g[0] = gvec[0]; C.g[1] = gvec[1]; C.g[2] = gvec[2];
   C.n_ckpt = (n_steps + ckpt - 1) / ckpt;
   C.n_rec = ckpt * n_sub;
   const size_t S = n_snakes, xs = S * n_max * 3, ps = S * l_max * 2;
-  ACU(cudaMalloc(&C.theta, S * 5 * sizeof(float)));
-  ACU(cudaMalloc(&C.x, xs * sizeof(float)));
-  ACU(cudaMalloc(&C.v, xs * sizeof(float)));
-  ACU(cudaMalloc(&C.p, ps * sizeof(float)));
-  ACU(cudaMalloc(&C.ck_x, C.n_ckpt * xs * sizeof(float)));
-  ACU(cudaMalloc(&C.ck_v, C.n_ckpt * xs * sizeof(float)));
-  ACU(cudaMalloc(&C.ck_p, C.n_ckpt * ps * sizeof(float)));
+  ACU(C.grow(kTheta, S * 5));
+  ACU(C.grow(kX, xs));
+  ACU(C.grow(kV, xs));
+  ACU(C.grow(kP, ps));
+  ACU(C.grow(kCkX, C.n_ckpt * xs));
+  ACU(C.grow(kCkV, C.n_ckpt * xs));
+  ACU(C.grow(kCkP, C.n_ckpt * ps));
   ACU(cudaMemcpyAsync(C.theta, theta, S * 5 * sizeof(float), cudaMemcpyDeviceToDevice, st));
   C.smem = adjoint_smem_bytes(n_max, l_max);
   ACU(cudaFuncSetAttribute(adj_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C.smem));
@@ -711,15 +728,13 @@ SimStatus calib_backward(CalibState& C, const SnakeParams* prm, const int* no, c
                          const float* tips_bar, float* grad, cudaStream_t st, std::string& err) {
   if (C.n_steps <= 0) { err = "no calibration forward pass to differentiate"; return SIM_EINVAL; }
   const size_t S = C.n_snakes, xs = S * C.n_max * 3, ps = S * C.l_max * 2;
-  if (!C.rec_x) {
-    ACU(cudaMalloc(&C.rec_x, S * C.n_rec * C.n_max * 3 * sizeof(float)));
-    ACU(cudaMalloc(&C.rec_v, S * C.n_rec * C.n_max * 3 * sizeof(float)));
-    ACU(cudaMalloc(&C.rec_p, S * C.n_rec * C.l_max * 2 * sizeof(float)));
-    ACU(cudaMalloc(&C.iters, S * (C.K + 1) * C.n_max * 9 * sizeof(float)));
-    ACU(cudaMalloc(&C.xb, xs * sizeof(float)));
-    ACU(cudaMalloc(&C.vb, xs * sizeof(float)));
-    ACU(cudaMalloc(&C.pb, ps * sizeof(float)));
-  }
+  ACU(C.grow(kRecX, S * C.n_rec * C.n_max * 3));
+  ACU(C.grow(kRecV, S * C.n_rec * C.n_max * 3));
+  ACU(C.grow(kRecP, S * C.n_rec * C.l_max * 2));
+  ACU(C.grow(kIters, S * (C.K + 1) * C.n_max * 9));
+  ACU(C.grow(kXb, xs));
+  ACU(C.grow(kVb, xs));
+  ACU(C.grow(kPb, ps));
   ACU(cudaMemsetAsync(C.xb, 0, xs * sizeof(float), st));
   ACU(cudaMemsetAsync(C.vb, 0, xs * sizeof(float), st));
   ACU(cudaMemsetAsync(C.pb, 0, ps * sizeof(float), st));

@@ -17,6 +17,22 @@ constexpr int layout_lanes(int id) { return 8 << (id / 4); }
 constexpr int layout_npl(int id) { return id % 4 + 1; }
 constexpr int kNumLayouts = 12;
 
+// Row slot k of node i (six per node: stretch to i + 1, yaw and pitch bend centred on
+// i, contact, friction x / y) of a snake of N nodes whose first nfix nodes are held:
+// whether the row exists, i.e. whether its warm-start features carry a row kind.
+__host__ __device__ inline bool feature_row_exists(int i, int k, int N, int nfix, int contact) {
+  if (k == 0) return i + 1 <= N - 1;
+  if (k <= 2) return i >= 1 && i + 1 <= N - 1;
+  return contact != 0 && i >= nfix;
+}
+// Existing rows of the node slots before node i (node by node, kinds in order).
+__host__ __device__ inline int feature_rows_before(int i, int N, int nfix, int contact) {
+  const int st = i < N - 1 ? i : N - 1;   // stretch rows of nodes 0 .. min(i, N - 1) - 1
+  const int bd = st > 1 ? st - 1 : 0;     // bend pairs of nodes 1 .. min(i, N - 1) - 1
+  const int ct = contact != 0 && i > nfix ? i - nfix : 0;
+  return st + 2 * bd + 3 * ct;
+}
+
 struct SolverArgs {
   float4* pos;            // [nodes] x, y, z, inverse mass
   float4* vel;            // [nodes] vx, vy, vz, 0

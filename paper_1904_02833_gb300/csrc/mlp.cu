@@ -8,6 +8,7 @@
 // layout (tc.cuh); transposed operands of the weight gradients are written transposed
 // by the epilogue threads, so every MMA reads K-major tiles.  Adam runs on FP32 master
 // weights (mlp_adam_kernel) and refreshes the BF16 copies the GEMMs read.
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -41,6 +42,19 @@ constexpr int kOffW3 = kOffB2 + kHid;
 constexpr int kOffB3 = kOffW3 + kHid;
 constexpr int kNumParams = kOffB3 + 1;  // 19841
 static_assert(kNumParams == MLP_NUM_PARAMS, "parameter count");
+
+// After a timed-out wait on an MMA: thread 0, the only thread that issues MMAs, commits
+// once more to a barrier of its own, which arrives only when every MMA the thread issued
+// before has completed (tcgen05.commit tracks all of the issuing thread's earlier
+// tensor-core operations, not one group), and the block waits for that arrival before
+// its TMEM columns are freed.  Like every wait it is bounded: an MMA completes in
+// microseconds, so a drain that runs out means no completion will ever arrive (the
+// columns are not being written) and the block still frees them, which it must do
+// before it exits.
+__device__ __forceinline__ void drain_mma(uint64_t* drain, int t) {
+  if (t == 0) tc::mma_commit(drain);
+  tc::mbar_wait(drain, 0, kWaitLimit);
+}
 
 struct MlpDev {
   const __nv_bfloat16* w1;  // [128][32] row-major (out x in, zero-padded in 24..31)
@@ -112,6 +126,7 @@ struct InferSmem {
   float b1[kHid], b2[kHid], w3[kHid];
   float part[kTile];  // second column half's share of y, per row
   uint64_t mbar;
+  uint64_t drain;  // drain_mma: arrives once every MMA issued so far has completed
   uint32_t tmem;
 };
 constexpr int kInferThreads = 256;
@@ -132,7 +147,7 @@ __global__ void __launch_bounds__(kInferThreads, 2) mlp_infer_kernel(const __nv_
   const int quad = warp & 3, half = warp >> 2;
   const int row = quad * 32 + lane;  // the TMEM lane (tile row) this thread reads
   if (warp == 0) tc::tmem_alloc(&S.tmem, 256);
-  if (t == 0) tc::mbar_init(&S.mbar, 1);
+  if (t == 0) { tc::mbar_init(&S.mbar, 1); tc::mbar_init(&S.drain, 1); }
   stage_kmajor(S.w1, w.w1, kHid, kInPad);
   stage_kmajor(S.w2, w.w2, kHid, kHid);
   if (t < kHid) { S.b1[t] = w.b1[t]; S.b2[t] = w.b2[t]; S.w3[t] = w.w3[t]; }
@@ -231,7 +246,7 @@ __global__ void __launch_bounds__(kInferThreads, 2) mlp_infer_kernel(const __nv_
   }
   if (!ok) {
     if (t == 0) atomicExch(err, 1);
-    tc::mbar_wait(&S.mbar, phase, kWaitLimit);  // let an MMA in flight finish
+    drain_mma(&S.drain, t);
   }
   tc::fence_before_sync();
   __syncthreads();
@@ -253,6 +268,7 @@ struct TrainSmem {
   float gb1[kHid], gb2[kHid], gw3[kHid];
   float gb3, loss;
   uint64_t mbar;
+  uint64_t drain;  // drain_mma: arrives once every MMA issued so far has completed
   uint32_t tmem;
 };
 
@@ -269,7 +285,7 @@ __global__ void __launch_bounds__(128, 1) mlp_train_kernel(const __nv_bfloat16* 
   TrainSmem& S = *reinterpret_cast<TrainSmem*>(smem_raw);
   const int t = threadIdx.x, warp = t >> 5;
   if (warp == 0) tc::tmem_alloc(&S.tmem, 512);
-  if (t == 0) { tc::mbar_init(&S.mbar, 1); S.gb3 = 0.f; S.loss = 0.f; }
+  if (t == 0) { tc::mbar_init(&S.mbar, 1); tc::mbar_init(&S.drain, 1); S.gb3 = 0.f; S.loss = 0.f; }
   stage_kmajor(S.w1, w.w1, kHid, kInPad);
   stage_kmajor(S.w2, w.w2, kHid, kHid);
   stage_kmajor_t(S.w2t, w.w2, kHid, kHid);
@@ -431,7 +447,7 @@ __global__ void __launch_bounds__(128, 1) mlp_train_kernel(const __nv_bfloat16* 
     __syncthreads();
     tc::fence_after_sync();
   }
-  if (!ok) tc::mbar_wait(&S.mbar, phase, kWaitLimit);
+  if (!ok) drain_mma(&S.drain, t);
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
@@ -598,6 +614,7 @@ SimStatus mlp_get_params(MlpHandle* h, float* params, int is_device) {
 
 SimStatus mlp_forward(MlpHandle* h, const void* feat, int64_t rows, float* out) {
   if (!h || !feat || !out || rows < 0) return mfail(SIM_EINVAL, "bad arguments");
+  if (((uintptr_t)feat & 15u) != 0) return mfail(SIM_EINVAL, "feat is not 16-byte aligned");
   SimStatus s = snakesim::mlp_forward_launch(h, feat, rows, out, h->stream);
   if (s != SIM_OK) return s;
   return check_err(h);
@@ -606,6 +623,7 @@ SimStatus mlp_forward(MlpHandle* h, const void* feat, int64_t rows, float* out) 
 SimStatus mlp_grad(MlpHandle* h, const void* feat, const float* target, int64_t rows, float scale,
                    float* grad, float* loss) {
   if (!h || !feat || !target || rows < 0) return mfail(SIM_EINVAL, "bad arguments");
+  if (((uintptr_t)feat & 15u) != 0) return mfail(SIM_EINVAL, "feat is not 16-byte aligned");
   MCU(cudaMemsetAsync(h->g, 0, kNumParams * sizeof(float), h->stream));
   MCU(cudaMemsetAsync(h->loss, 0, sizeof(float), h->stream));
   if (rows > 0) {
@@ -623,6 +641,7 @@ SimStatus mlp_grad(MlpHandle* h, const void* feat, const float* target, int64_t 
 SimStatus mlp_train_step(MlpHandle* h, const void* feat, const float* target, int64_t rows, float lr,
                          float* loss) {
   if (!h || !feat || !target || rows <= 0 || !(lr > 0.f)) return mfail(SIM_EINVAL, "bad arguments");
+  if (((uintptr_t)feat & 15u) != 0) return mfail(SIM_EINVAL, "feat is not 16-byte aligned");
   MCU(cudaMemsetAsync(h->g, 0, kNumParams * sizeof(float), h->stream));
   MCU(cudaMemsetAsync(h->loss, 0, sizeof(float), h->stream));
   const long long tiles = (rows + kTile - 1) / kTile;
@@ -674,24 +693,58 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
 constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mu;
 unsigned char* g_noalloc_addr[kMaxDevices] = {};  // device address of the array, per device
+unsigned long long g_noalloc_ctx[kMaxDevices] = {};  // id of the context it belongs to
 int g_noalloc_sms[kMaxDevices] = {};
 
-// Once per device, with that device current: the array's device address (the name
-// g_noalloc_scratch in host code is only a host-side stand-in) and the kernel's
-// shared-memory opt-in.
+// The id of the calling thread's current CUDA context (0 if none yet), from the driver's
+// cuCtxGetCurrent / cuCtxGetId, reached through the runtime's driver entry points (no
+// link-time dependency on the driver library).  The driver never reuses an id, so a
+// primary context destroyed by cudaDeviceReset and created again has a new one.
+SimStatus current_context_id(unsigned long long* id) {
+  typedef CUresult (*GetCur)(CUcontext*);
+  typedef CUresult (*GetId)(CUcontext, unsigned long long*);
+  static GetCur get_cur = nullptr;
+  static GetId get_id = nullptr;
+  if (!get_cur || !get_id) {
+    cudaDriverEntryPointQueryResult q1 = cudaDriverEntryPointSymbolNotFound, q2 = q1;
+    void *f1 = nullptr, *f2 = nullptr;
+    cudaError_t e1 = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1);
+    cudaError_t e2 = cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2);
+    if (e1 != cudaSuccess || e2 != cudaSuccess || q1 != cudaDriverEntryPointSuccess ||
+        q2 != cudaDriverEntryPointSuccess || !f1 || !f2)
+      return mfail(SIM_ECUDA, "cuCtxGetCurrent / cuCtxGetId entry points not available");
+    get_cur = reinterpret_cast<GetCur>(f1);
+    get_id = reinterpret_cast<GetId>(f2);
+  }
+  CUcontext c = nullptr;
+  if (get_cur(&c) != CUDA_SUCCESS) return mfail(SIM_ECUDA, "cuCtxGetCurrent failed");
+  *id = 0;
+  if (c && get_id(c, id) != CUDA_SUCCESS) return mfail(SIM_ECUDA, "cuCtxGetId failed");
+  return SIM_OK;
+}
+
+// Set-up, once per device and context, with that device current: the array's device
+// address (the name g_noalloc_scratch in host code is only a host-side stand-in) and the
+// kernel's shared-memory opt-in.  A later context on the device (after cudaDeviceReset)
+// is set up again.
 SimStatus noalloc_setup(int dev, unsigned char** addr, int* sms) {
   std::lock_guard<std::mutex> lock(g_noalloc_mu);
-  if (!g_noalloc_addr[dev]) {
+  unsigned long long ctx = 0;
+  SimStatus s = current_context_id(&ctx);
+  if (s != SIM_OK) return s;
+  if (!g_noalloc_addr[dev] || ctx == 0 || ctx != g_noalloc_ctx[dev]) {
     void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);  // creates the context if needed
     if (e != cudaSuccess) return mfail(SIM_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
     e = cudaFuncSetAttribute(mlp_infer_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(InferSmem));
     if (e != cudaSuccess) return mfail(SIM_ECUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e));
     int n = 0;
     e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return mfail(SIM_ECUDA, std::string("cudaDeviceGetAttribute: ") + cudaGetErrorString(e));
+    if (ctx == 0 && (s = current_context_id(&ctx)) != SIM_OK) return s;
     g_noalloc_sms[dev] = n;
     g_noalloc_addr[dev] = static_cast<unsigned char*>(p);
+    g_noalloc_ctx[dev] = ctx;
   }
   *addr = g_noalloc_addr[dev];
   *sms = g_noalloc_sms[dev];
@@ -702,6 +755,7 @@ SimStatus noalloc_setup(int dev, unsigned char** addr, int* sms) {
 extern "C" SimStatus mlp_forward_noalloc(const float* params, int32_t n_params, const void* feat,
                                          int64_t rows, float* out, void* stream) {
   if (!params || !feat || !out || rows < 0) return mfail(SIM_EINVAL, "null pointer or rows < 0");
+  if (((uintptr_t)feat & 15u) != 0) return mfail(SIM_EINVAL, "feat is not 16-byte aligned");
   if (n_params != kNumParams)
     return mfail(SIM_EINVAL, "mlp_forward_noalloc: its static working array holds the bfloat16 weights of "
                              "exactly one 24-128-128-1 network (" + std::to_string(kNumParams) +

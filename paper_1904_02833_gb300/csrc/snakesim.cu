@@ -56,8 +56,13 @@ namespace {
 // instructions, against under one with a kernel per layout.)  The host launches the
 // layouts that have work on forked streams, so that the next layout fills the tail of the
 // previous one.
+// Two blocks of four warps per SM leave the compiler up to 255 registers per thread to
+// overlap the independent node slots of a lane's pass (the pass is latency-bound: with
+// few warps per scheduler, a warp's own instruction-level parallelism sets its speed).
+// Measured against three blocks (168 registers): 16384 snakes 2-5 % faster per env-step,
+// 4096 snakes 15-39 % faster.
 #ifndef SNAKE_MIN_BLOCKS
-#define SNAKE_MIN_BLOCKS 3
+#define SNAKE_MIN_BLOCKS 2
 #endif
 // Persistent: every warp takes the next work item (32/G snakes of one node count) from
 // the layout's counter in global memory until none is left.
@@ -198,6 +203,37 @@ __global__ void unpack_xyz_kernel(const float* __restrict__ in, float4* __restri
   }
 }
 
+// Training rows of the learned warm start (sim_training_rows): one warp per snake, lanes
+// over its nodes.  Every existing row (feature_row_exists) of node i goes to output row
+// out_off[s] + feature_rows_before(i) + (existing kinds of node i before k): its features
+// are copied and its target is (lam_star - beta lam_prev) / (m g h^2), the network's
+// output that would turn the warm start beta lam_prev + m g h^2 y into lam_star.
+__global__ void training_rows_kernel(const __nv_bfloat16* __restrict__ feat, const int* __restrict__ feat_off,
+                                     const int* __restrict__ node_off, const SnakeParams* __restrict__ prm,
+                                     const long long* __restrict__ out_off, const float* __restrict__ lam_star,
+                                     const float* __restrict__ lam_prev, float beta, float h, int contact,
+                                     int n, __nv_bfloat16* __restrict__ feat_out, float* __restrict__ target_out) {
+  const int s = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (s >= n) return;
+  const SnakeParams P = prm[s];
+  const int N = P.n_links * P.seg_per_link + 1;
+  const float inv = 1.0f / (P.mass * 9.81f * h * h);
+  for (int i = lane; i < N; i += 32) {
+    long long o = out_off[s] + feature_rows_before(i, N, P.n_fixed, contact);
+    const long long g = (long long)node_off[s] + i;
+    for (int k = 0; k < 6; ++k) {
+      if (!feature_row_exists(i, k, N, P.n_fixed, contact)) continue;
+      const uint4* src = reinterpret_cast<const uint4*>(feat + ((long long)(feat_off[s] + i) * 6 + k) * 32);
+      uint4* dst = reinterpret_cast<uint4*>(feat_out + o * 32);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) dst[c] = src[c];
+      target_out[o] = (lam_star[g * 6 + k] - beta * lam_prev[g * 6 + k]) * inv;
+      ++o;
+    }
+  }
+}
+
 // ------------------------------------------------------------------ handle
 struct SimHandle {
   SimConfig cfg;
@@ -255,6 +291,11 @@ struct SimHandle {
   float4 *snap_pos = nullptr, *snap_vel = nullptr;
   float2* snap_press = nullptr;
   float* snap_lam = nullptr;
+  float* snap_resid = nullptr;           // per-snake residual / update count / status
+  int *snap_iters = nullptr, *snap_status = nullptr;
+  __nv_bfloat16* snap_feat = nullptr;    // features of a begun substep (split stepping)
+  long long* train_off = nullptr;        // sim_training_rows: first output row per snake
+  std::vector<long long> train_off_h;
   long long snap_step = 0;
   long long* snap_step_dev = nullptr;
   int snap_sub = -1;
@@ -904,74 +945,88 @@ SimStatus sim_set_layout(SimHandle* h, int nodes, int lanes, int npl) {
 SimStatus sim_autotune(SimHandle* h, int n_steps) {
   if (!h) return fail(SIM_EINVAL, "null handle");
   if (n_steps < 1) return fail(SIM_EINVAL, "n_steps < 1");
-  // save the state, time every admissible layout of every bucket alone, restore
+  if (h->cur_sub >= 0) return fail(SIM_EINVAL, "a split env-step is in progress (sim_split_finish)");
+  // save the state, time every admissible layout of every bucket alone, restore; every
+  // exit goes through `finish`, which frees what was taken, puts the state back and
+  // rebuilds the work items of all buckets (with the best layouts, or the old ones on error)
   const long long n = h->n_nodes;
   float4 *p0 = nullptr, *v0 = nullptr;
   float2* pr0 = nullptr;
-  float* l0 = nullptr;
-  CU(cudaMalloc(&p0, n * sizeof(float4)));
-  CU(cudaMalloc(&v0, n * sizeof(float4)));
-  CU(cudaMalloc(&pr0, h->n_links * sizeof(float2)));
-  CU(cudaMalloc(&l0, n * 6 * sizeof(float)));
-  auto save = [&]() -> SimStatus {
-    CU(cudaMemcpyAsync(p0, h->pos, n * sizeof(float4), cudaMemcpyDeviceToDevice, h->stream));
-    CU(cudaMemcpyAsync(v0, h->vel, n * sizeof(float4), cudaMemcpyDeviceToDevice, h->stream));
-    CU(cudaMemcpyAsync(pr0, h->press, h->n_links * sizeof(float2), cudaMemcpyDeviceToDevice, h->stream));
-    CU(cudaMemcpyAsync(l0, h->lam, n * 6 * sizeof(float), cudaMemcpyDeviceToDevice, h->stream));
-    return SIM_OK;
-  };
+  float *l0 = nullptr, *r0 = nullptr;
+  int *i0 = nullptr, *s0 = nullptr;
+  cudaEvent_t a = nullptr, b = nullptr;
+  const std::map<int, int> layout0 = h->layout;
   const long long step_keep = h->step_index;
-  auto restore = [&]() -> SimStatus {
-    CU(cudaMemcpyAsync(h->step_dev, &step_keep, sizeof(long long), cudaMemcpyHostToDevice, h->stream));
-    CU(cudaMemcpyAsync(h->pos, p0, n * sizeof(float4), cudaMemcpyDeviceToDevice, h->stream));
-    CU(cudaMemcpyAsync(h->vel, v0, n * sizeof(float4), cudaMemcpyDeviceToDevice, h->stream));
-    CU(cudaMemcpyAsync(h->press, pr0, h->n_links * sizeof(float2), cudaMemcpyDeviceToDevice, h->stream));
-    CU(cudaMemcpyAsync(h->lam, l0, n * 6 * sizeof(float), cudaMemcpyDeviceToDevice, h->stream));
-    return SIM_OK;
+  SimStatus st = SIM_OK;
+  auto ok = [&](cudaError_t e, const char* what) {
+    if (e != cudaSuccess && st == SIM_OK)
+      st = fail(e == cudaErrorMemoryAllocation ? SIM_ENOMEM : SIM_ECUDA, std::string(what) + ": " +
+                cudaGetErrorString(e));
+    return st == SIM_OK;
   };
-  SimStatus st = save();
-  cudaEvent_t a, b;
-  CU(cudaEventCreate(&a));
-  CU(cudaEventCreate(&b));
-  std::map<int, int> best = h->layout;
-  std::vector<int> sizes;
-  for (auto& kv : h->layout) sizes.push_back(kv.first);
-  for (int N : sizes) {
+  auto copy = [&](void* dst, const void* src, size_t bytes, cudaMemcpyKind k) {
+    return ok(cudaMemcpyAsync(dst, src, bytes, k, h->stream), "autotune copy");
+  };
+  auto xfer = [&](bool save) {
+    const cudaMemcpyKind d2d = cudaMemcpyDeviceToDevice;
+    if (save) {
+      return copy(p0, h->pos, n * sizeof(float4), d2d) && copy(v0, h->vel, n * sizeof(float4), d2d) &&
+             copy(pr0, h->press, h->n_links * sizeof(float2), d2d) && copy(l0, h->lam, n * 6 * sizeof(float), d2d) &&
+             copy(r0, h->resid, h->n * sizeof(float), d2d) && copy(i0, h->iters, h->n * sizeof(int), d2d) &&
+             copy(s0, h->status, h->n * sizeof(int), d2d);
+    }
+    return copy(h->step_dev, &step_keep, sizeof(long long), cudaMemcpyHostToDevice) &&
+           copy(h->pos, p0, n * sizeof(float4), d2d) && copy(h->vel, v0, n * sizeof(float4), d2d) &&
+           copy(h->press, pr0, h->n_links * sizeof(float2), d2d) && copy(h->lam, l0, n * 6 * sizeof(float), d2d) &&
+           copy(h->resid, r0, h->n * sizeof(float), d2d) && copy(h->iters, i0, h->n * sizeof(int), d2d) &&
+           copy(h->status, s0, h->n * sizeof(int), d2d);
+  };
+  std::map<int, int> best = layout0;
+  bool saved = false;
+  if (ok(cudaMalloc(&p0, n * sizeof(float4)), "cudaMalloc") && ok(cudaMalloc(&v0, n * sizeof(float4)), "cudaMalloc") &&
+      ok(cudaMalloc(&pr0, h->n_links * sizeof(float2)), "cudaMalloc") &&
+      ok(cudaMalloc(&l0, n * 6 * sizeof(float)), "cudaMalloc") && ok(cudaMalloc(&r0, h->n * sizeof(float)), "cudaMalloc") &&
+      ok(cudaMalloc(&i0, h->n * sizeof(int)), "cudaMalloc") && ok(cudaMalloc(&s0, h->n * sizeof(int)), "cudaMalloc") &&
+      ok(cudaEventCreate(&a), "cudaEventCreate") && ok(cudaEventCreate(&b), "cudaEventCreate"))
+    saved = xfer(true);
+  for (auto it = layout0.begin(); st == SIM_OK && it != layout0.end(); ++it) {
+    const int N = it->first;
     float best_ms = 1e30f;
     for (int G : {8, 16, 32}) {
-      for (int npl = 1; npl <= 4; ++npl) {
+      for (int npl = 1; npl <= 4 && st == SIM_OK; ++npl) {
         if (G * npl < N || (npl > 1 && G * (npl - 1) >= N)) continue;  // no empty lanes column
         std::map<int, int> one;
         one[N] = layout_id(G, npl);
-        std::map<int, int> saved = h->layout;
+        h->layout = layout0;
         h->layout[N] = layout_id(G, npl);
-        st = build_items(h, &one);
-        if (st != SIM_OK) break;
+        if ((st = build_items(h, &one)) != SIM_OK) break;
         float ms = 0.f;
         for (int rep = 0; rep < 2 && st == SIM_OK; ++rep) {
-          if ((st = restore()) != SIM_OK) break;
-          CU(cudaEventRecord(a, h->stream));
-          st = launch_steps(h, n_steps, h->stream);
-          CU(cudaEventRecord(b, h->stream));
-          CU(cudaEventSynchronize(b));
-          CU(cudaEventElapsedTime(&ms, a, b));
+          if (!xfer(false) || !ok(cudaEventRecord(a, h->stream), "cudaEventRecord")) break;
+          if ((st = launch_steps(h, n_steps, h->stream)) != SIM_OK) break;
+          if (!ok(cudaEventRecord(b, h->stream), "cudaEventRecord") || !ok(cudaEventSynchronize(b), "cudaEventSynchronize") ||
+              !ok(cudaEventElapsedTime(&ms, a, b), "cudaEventElapsedTime"))
+            break;
         }
-        h->layout = saved;
-        if (st != SIM_OK) break;
-        if (ms < best_ms) { best_ms = ms; best[N] = layout_id(G, npl); }
+        if (st == SIM_OK && ms < best_ms) { best_ms = ms; best[N] = layout_id(G, npl); }
       }
-      if (st != SIM_OK) break;
     }
-    if (st != SIM_OK) break;
   }
-  if (st == SIM_OK) st = restore();
-  CU(cudaStreamSynchronize(h->stream));
-  cudaEventDestroy(a);
-  cudaEventDestroy(b);
-  cudaFree(p0); cudaFree(v0); cudaFree(pr0); cudaFree(l0);
-  if (st != SIM_OK) return st;
-  h->layout = best;
-  return build_items(h);
+  // finish: state back, buffers and events freed, all buckets' items rebuilt
+  const SimStatus run = st;
+  st = SIM_OK;
+  if (saved) xfer(false);
+  ok(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+  const SimStatus put_back = st;
+  if (a) cudaEventDestroy(a);
+  if (b) cudaEventDestroy(b);
+  for (void* q : {(void*)p0, (void*)v0, (void*)pr0, (void*)l0, (void*)r0, (void*)i0, (void*)s0})
+    if (q) cudaFree(q);
+  h->layout = run == SIM_OK ? best : layout0;
+  const SimStatus rebuilt = build_items(h);
+  if (run != SIM_OK) return run;
+  if (put_back != SIM_OK) return put_back;
+  return rebuilt;
 }
 
 SimStatus sim_set_mlp(SimHandle* h, MlpHandle* m) {
@@ -1021,6 +1076,37 @@ SimStatus sim_features(SimHandle* h, void** feat, int64_t* rows) {
   return SIM_OK;
 }
 
+SimStatus sim_training_rows(SimHandle* h, const float* lam_star, const float* lam_prev, float beta,
+                            void* feat_out, float* target_out, int64_t capacity, int64_t* n_rows) {
+  if (!h || !n_rows) return fail(SIM_EINVAL, "null handle or row count");
+  if (h->cur_sub < 0) return fail(SIM_EINVAL, "no substep in progress (sim_split_begin)");
+  const int contact = h->cfg.contact;
+  h->train_off_h.assign(h->n + 1, 0);
+  for (int s = 0; s < h->n; ++s) {
+    const SnakeParams& p = h->hprm[s];
+    const int N = p.n_links * p.seg_per_link + 1;
+    h->train_off_h[s + 1] = h->train_off_h[s] + feature_rows_before(N, N, p.n_fixed, contact);
+  }
+  const long long total = h->train_off_h[h->n];
+  *n_rows = total;
+  if (!feat_out && !target_out) return SIM_OK;  // count only
+  if (!feat_out || !target_out || !lam_star || !lam_prev)
+    return fail(SIM_EINVAL, "null feature, target or multiplier buffer");
+  if (capacity < total) return fail(SIM_EINVAL, "output capacity below the row count");
+  if (((uintptr_t)feat_out & 15u) != 0) return fail(SIM_EINVAL, "feat_out is not 16-byte aligned");
+  if (!(beta >= 0.f && beta <= 1.f)) return fail(SIM_EINVAL, "beta outside [0, 1]");
+  if (!h->train_off) CU(cudaMalloc(&h->train_off, (h->n + 1) * sizeof(long long)));
+  CU(cudaMemcpyAsync(h->train_off, h->train_off_h.data(), (h->n + 1) * sizeof(long long),
+                     cudaMemcpyHostToDevice, h->stream));
+  const int threads = 256, blocks = (int)((32LL * h->n + threads - 1) / threads);
+  training_rows_kernel<<<blocks, threads, 0, h->stream>>>(
+      h->feat, h->feat_off_d, h->node_off_d, h->prm, h->train_off, lam_star, lam_prev, beta,
+      (float)(h->cfg.dt / h->cfg.n_sub), contact, h->n, (__nv_bfloat16*)feat_out, target_out);
+  CU(cudaGetLastError());
+  h->launches += 1;
+  return SIM_OK;
+}
+
 SimStatus sim_snapshot_save(SimHandle* h) {
   if (!h) return fail(SIM_EINVAL, "null handle");
   const long long n = h->n_nodes;
@@ -1036,6 +1122,21 @@ SimStatus sim_snapshot_save(SimHandle* h) {
   CU(cudaMemcpyAsync(h->snap_vel, h->vel, n * sizeof(float4), cudaMemcpyDeviceToDevice, h->stream));
   CU(cudaMemcpyAsync(h->snap_press, h->press, h->n_links * sizeof(float2), cudaMemcpyDeviceToDevice, h->stream));
   CU(cudaMemcpyAsync(h->snap_lam, h->lam, n * 6 * sizeof(float), cudaMemcpyDeviceToDevice, h->stream));
+  // split stepping carries the step's residual and update count from launch to launch,
+  // and the next launch of a begun substep reads its features
+  if (!h->snap_resid) {
+    CU(cudaMalloc(&h->snap_resid, h->n * sizeof(float)));
+    CU(cudaMalloc(&h->snap_iters, h->n * sizeof(int)));
+    CU(cudaMalloc(&h->snap_status, h->n * sizeof(int)));
+  }
+  CU(cudaMemcpyAsync(h->snap_resid, h->resid, h->n * sizeof(float), cudaMemcpyDeviceToDevice, h->stream));
+  CU(cudaMemcpyAsync(h->snap_iters, h->iters, h->n * sizeof(int), cudaMemcpyDeviceToDevice, h->stream));
+  CU(cudaMemcpyAsync(h->snap_status, h->status, h->n * sizeof(int), cudaMemcpyDeviceToDevice, h->stream));
+  if (h->cur_sub >= 0) {
+    if (!h->snap_feat) CU(cudaMalloc(&h->snap_feat, n * 6 * 32 * sizeof(__nv_bfloat16)));
+    CU(cudaMemcpyAsync(h->snap_feat, h->feat, n * 6 * 32 * sizeof(__nv_bfloat16), cudaMemcpyDeviceToDevice,
+                       h->stream));
+  }
   h->snap_step = h->step_index;
   h->snap_sub = h->cur_sub;
   h->snap_valid = true;
@@ -1051,6 +1152,12 @@ SimStatus sim_snapshot_restore(SimHandle* h) {
   CU(cudaMemcpyAsync(h->press, h->snap_press, h->n_links * sizeof(float2), cudaMemcpyDeviceToDevice, h->stream));
   CU(cudaMemcpyAsync(h->lam, h->snap_lam, n * 6 * sizeof(float), cudaMemcpyDeviceToDevice, h->stream));
   CU(cudaMemcpyAsync(h->step_dev, h->snap_step_dev, sizeof(long long), cudaMemcpyDeviceToDevice, h->stream));
+  CU(cudaMemcpyAsync(h->resid, h->snap_resid, h->n * sizeof(float), cudaMemcpyDeviceToDevice, h->stream));
+  CU(cudaMemcpyAsync(h->iters, h->snap_iters, h->n * sizeof(int), cudaMemcpyDeviceToDevice, h->stream));
+  CU(cudaMemcpyAsync(h->status, h->snap_status, h->n * sizeof(int), cudaMemcpyDeviceToDevice, h->stream));
+  if (h->snap_sub >= 0)
+    CU(cudaMemcpyAsync(h->feat, h->snap_feat, n * 6 * 32 * sizeof(__nv_bfloat16), cudaMemcpyDeviceToDevice,
+                       h->stream));
   h->step_index = h->snap_step;
   h->cur_sub = h->snap_sub;
   return SIM_OK;
@@ -1117,6 +1224,31 @@ SimStatus sim_kernel_times(SimHandle* h, float* ms, int64_t* launches) {
   return st;
 }
 
+SimStatus sim_partition(int n_snakes, const SnakeParams* params, int parts, int32_t* first) {
+  if (n_snakes < 1 || parts < 1 || !params || !first) return fail(SIM_EINVAL, "n_snakes, parts >= 1 and buffers");
+  std::vector<long long> pre(n_snakes + 1, 0);
+  for (int s = 0; s < n_snakes; ++s) {
+    if (params[s].n_links < 1 || params[s].seg_per_link < 1)
+      return fail(SIM_EINVAL, "snake " + std::to_string(s) + " has no links or segments");
+    pre[s + 1] = pre[s] + (long long)params[s].n_links * params[s].seg_per_link + 1;
+  }
+  const long long total = pre[n_snakes];
+  first[0] = 0;
+  int s = 0;
+  for (int p = 1; p < parts; ++p) {
+    // nearest boundary to p / parts of the total: |parts pre[s] - p total| smallest
+    const long long target = (long long)p * total;
+    while (s < n_snakes && (long long)parts * pre[s + 1] <= target) ++s;
+    if (s < n_snakes) {
+      const long long below = target - (long long)parts * pre[s], above = (long long)parts * pre[s + 1] - target;
+      if (above < below) ++s;
+    }
+    first[p] = std::max(first[p - 1], s);
+  }
+  first[parts] = n_snakes;
+  return SIM_OK;
+}
+
 SimStatus sim_destroy(SimHandle* h) {
   if (!h) return SIM_OK;
   cudaStreamSynchronize(h->stream);
@@ -1135,7 +1267,8 @@ SimStatus sim_destroy(SimHandle* h) {
                   h->iters, h->status, h->items, h->order, h->ucmd, h->inv_mass_d, h->scratch3,
                   h->lam0, h->feat, h->snap_pos, h->snap_vel, h->snap_press, h->snap_lam,
                   h->step_dev, h->snap_step_dev, h->work, h->sched_cls, h->sched_base,
-                  h->sched_hist, h->sched_key, h->items0, h->feat_off_d};
+                  h->sched_hist, h->sched_key, h->items0, h->feat_off_d, h->snap_resid,
+                  h->snap_iters, h->snap_status, h->snap_feat, h->train_off};
   for (void* p : ptrs) if (p) cudaFree(p);
   delete h;
   return SIM_OK;

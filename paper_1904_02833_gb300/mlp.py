@@ -97,16 +97,13 @@ def collect(sim, n_steps: int, substeps=None, every: int = 1, target_tol: float 
     tolerance, warm start and, in the learned mode, its network), so the features carry
     the previous multipliers the deployed solver produces.  At each logged substep the
     substep is also solved from the same start to `target_tol` (cold start) on a
-    snapshot; the target of a row is its multiplier there over m g h^2 minus beta times
-    the previous multiplier over m g h^2 (the network predicts the correction to the
-    beta-weighted previous multiplier).  Returns bf16 features [n, 32] and float targets
-    [n] of the existing rows, on the device."""
+    snapshot; sim_training_rows then writes every existing row's features and its target
+    (the multiplier reached there minus beta times the previous multiplier, over
+    m g h^2: the network predicts the correction to the beta-weighted previous
+    multiplier).  Returns bf16 features [n, 32] and float targets [n], on the device."""
     w = dict(sim.settings)
     n_sub = w["n_sub"]
-    h = w["dt"] / n_sub
     beta = float(w.get("beta", 1.0)) if skip is None else float(skip)
-    mass = torch.as_tensor(np.repeat(np.asarray(sim._mass_per_node, np.float32), 6), device=sim.device)
-    inv = 1.0 / (mass * 9.81 * h * h)
     target_cfg = dict(w, tol=float(target_tol), iters=int(target_iters), warm=0)
     feats, targets = [], []
     substeps = list(range(n_sub)) if substeps is None else list(substeps)
@@ -115,17 +112,16 @@ def collect(sim, n_steps: int, substeps=None, every: int = 1, target_tol: float 
         sim.split_begin()
         for s in range(n_sub):
             if log and s in substeps:
-                f = sim.features().clone()
-                lam_prev = sim.lam().reshape(-1).clone()
+                lam_prev = sim.lam().clone()
                 sim.snapshot_save()
                 sim.set_config(**target_cfg)
                 sim.split_finish()
-                lam_star = sim.lam().reshape(-1).clone()
+                lam_star = sim.lam().clone()
                 sim.snapshot_restore()
                 sim.set_config(**w)
-                keep = f[:, :6].float().sum(1) > 0
-                feats.append(f[keep])
-                targets.append(((lam_star - beta * lam_prev) * inv)[keep])
+                f, t = sim.training_rows(lam_star, lam_prev, beta)
+                feats.append(f)
+                targets.append(t)
             sim.split_finish()
     return torch.cat(feats), torch.cat(targets)
 

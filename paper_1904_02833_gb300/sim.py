@@ -62,6 +62,15 @@ def make_config(s: dict) -> N.SimConfig:
     return c
 
 
+def partition(w: dict, parts: int) -> np.ndarray:
+    """Contiguous snake ranges of a batch for `parts` GPUs, balanced by node count
+    (sim_partition): part p owns snakes [first[p], first[p + 1])."""
+    first = np.zeros(parts + 1, np.int32)
+    params = make_params(w)
+    N.check(N.load().sim_partition(len(w["n_links"]), params, int(parts), first.ctypes.data_as(ctypes.c_void_p)))
+    return first
+
+
 class SnakeSim:
     """A batch of snakes stepped on the GPU by libsnakesim."""
 
@@ -84,7 +93,6 @@ class SnakeSim:
         self.n_nodes, self.n_links = nn.value, nl.value
         nodes = np.asarray(w["n_links"], np.int64) * np.asarray(w["seg_per_link"]) + 1
         self.node_off = np.concatenate([[0], np.cumsum(nodes)])
-        self._mass_per_node = np.repeat(np.asarray(w["mass"], np.float64), nodes)
         self.link_off = np.concatenate([[0], np.cumsum(w["n_links"])])
 
     # ------------------------------------------------------------------ stepping
@@ -169,6 +177,19 @@ class SnakeSim:
         N.check(self.lib.sim_get_lambda(self.h, _ptr(out), 1))
         return out
 
+    def set_state_host(self, pos, vel, press, lam):
+        """State from host buffers (numpy arrays or pinned CPU tensors, float32, contiguous)
+        through the C-ABI's host path (is_device = 0)."""
+        p = [ctypes.c_void_p(a.data_ptr()) if isinstance(a, torch.Tensor) else a.ctypes.data_as(ctypes.c_void_p)
+             for a in (pos, vel, press, lam)]
+        N.check(self.lib.sim_set_state(self.h, p[0], p[1], p[2], p[3], 0))
+
+    def get_state_host(self, pos, vel, press, lam, resid=None, iters=None):
+        """State into host buffers (pinned CPU tensors, float32 / int32 for iters) through
+        the C-ABI's host path (is_device = 0); synchronises the stream."""
+        N.check(self.lib.sim_get_state(self.h, _ptr(pos), _ptr(vel), _ptr(press), _ptr(resid), _ptr(iters), 0))
+        N.check(self.lib.sim_get_lambda(self.h, _ptr(lam), 0))
+
     def set_state(self, pos=None, vel=None, press=None, lam=None):
         conv = lambda t: None if t is None else torch.as_tensor(t).to(self.device, torch.float32).contiguous()
         pos, vel, press, lam = conv(pos), conv(vel), conv(press), conv(lam)
@@ -206,6 +227,20 @@ class SnakeSim:
         rows = np.diff(self.node_off) * 6
         idx = np.repeat(first.astype(np.int64) - 6 * self.node_off[:-1], rows) + np.arange(6 * self.n_nodes)
         return buf[torch.as_tensor(idx, device=self.device)]
+
+    def training_rows(self, lam_star: torch.Tensor, lam_prev: torch.Tensor, beta: float):
+        """Features [rows, 32] bf16 and targets [rows] float of the existing rows of the
+        substep in progress (sim_training_rows), on the device."""
+        n = ctypes.c_int64()
+        N.check(self.lib.sim_training_rows(self.h, None, None, 0.0, None, None, 0, ctypes.byref(n)))
+        feat = torch.empty(n.value, 32, dtype=torch.bfloat16, device=self.device)
+        target = torch.empty(n.value, dtype=torch.float32, device=self.device)
+        a, b = lam_star.contiguous(), lam_prev.contiguous()
+        assert a.dtype == b.dtype == torch.float32 and a.numel() == b.numel() == 6 * self.n_nodes
+        N.check(self.lib.sim_training_rows(self.h, _ptr(a), _ptr(b), float(beta), _ptr(feat), _ptr(target),
+                                           n.value, ctypes.byref(n)))
+        self._train_keep = (a, b)
+        return feat, target
 
     def status(self):
         st = np.zeros(self.n, np.int32)

@@ -186,3 +186,78 @@ def test_trained_warm_start_needs_fewer_updates_than_cold_start():
             its.append(st["iters"].mean())
         res[mode] = float(np.mean(its))
     assert res["learned"] < 0.8 * res["cold"], res
+
+
+def _mid_step(w, s, subs=2):
+    from paper_1904_02833_gb300.sim import SnakeSim
+    g = SnakeSim(w, s)
+    g.step(3)
+    g.split_begin()
+    for _ in range(subs):
+        g.split_finish()
+    return g
+
+
+@pytest.mark.parametrize("contact", [True, False])
+def test_training_rows_match_oracle(contact):
+    """sim_training_rows against the oracle's definition of the training rows on the same
+    features and multipliers: the same rows in the same order, features bit for bit,
+    targets (lambda* - beta lambda_prev) / (m g h^2) to FP32 rounding; snakes with held
+    nodes and uneven masses included."""
+    w = W.batched(n=21, seed=34, links=(1, 8))
+    w["n_fixed"][:5] = [0, 1, 2, 3, 0]
+    w["mass"][::3] = 0.02
+    beta = 0.5
+    s = W.solver_settings(iters=5000, tol=1e-4, warm=1, beta=beta, contact=contact)
+    g = _mid_step(w, s)
+    lam_prev = g.lam().clone()
+    fnode = g.features().float().cpu().numpy()
+    g.snapshot_save()
+    g.set_config(tol=1e-6, iters=20000, warm=0)
+    g.split_finish()
+    lam_star = g.lam().clone()
+    g.snapshot_restore()
+    g.set_config(**s)
+    F, T = g.training_rows(lam_star, lam_prev, beta)
+    F, T = F.float().cpu().numpy(), T.cpu().numpy()
+    h = s["dt"] / s["n_sub"]
+    Fo, To = M.training_rows(g.node_off, w["mass"], fnode, lam_star.cpu().numpy().astype(np.float64),
+                             lam_prev.cpu().numpy().astype(np.float64), beta, h)
+    assert F.shape == Fo.shape and len(T) == len(To) > 0
+    assert np.array_equal(F, Fo)
+    scale = (np.abs(lam_star.cpu().numpy()).max() + np.abs(lam_prev.cpu().numpy()).max()) / (w["mass"].min() * 9.81 * h * h)
+    assert np.abs(T - To).max() <= 1e-6 * scale
+    # the restored features are the begun substep's, not those the branch wrote
+    assert np.array_equal(g.features().float().cpu().numpy(), fnode)
+
+
+def test_snapshot_branch_inside_a_split_step_is_invisible():
+    """Saving inside a split env-step, finishing the substep with another configuration,
+    restoring and finishing it in the learned mode gives, bit for bit, what a run that
+    never branched gives (state, multipliers, residuals and update counts)."""
+    w = W.batched(n=30, seed=35, links=(1, 8))
+    p = M.init_params(8) * 0.5
+    s = W.solver_settings(iters=5000, tol=1e-4, warm=2, beta=0.5)
+    net = mlp(p)
+    runs = []
+    for branch in (False, True):
+        from paper_1904_02833_gb300.sim import SnakeSim
+        g = SnakeSim(w, dict(s, warm=0))
+        g.step(2)
+        g.set_mlp(net)
+        g.set_config(**s)
+        g.split_begin()
+        for sub in range(s["n_sub"]):
+            if branch and sub in (1, 7):
+                g.snapshot_save()
+                g.set_config(tol=1e-6, iters=20000, warm=0)
+                g.split_finish()
+                g.snapshot_restore()
+                g.set_config(**s)
+            g.split_finish()
+        st = g.state_host()
+        st["lam"] = g.lam().cpu().numpy()
+        runs.append(st)
+        g.close()
+    for k in runs[0]:
+        assert np.array_equal(runs[0][k], runs[1][k]), k

@@ -93,3 +93,33 @@ def test_friction_row_frame_is_world_aligned():
     assert F[4, 4, 13:15] == pytest.approx([0.0, 0.3 * h / L0])
     assert F[4, 5, 13:15] == pytest.approx([0.3 * h / L0, 0.0])
     assert F[4, 1, 22] == pytest.approx(20.0 * 0.5 * L0)
+
+
+@pytest.mark.parametrize("beta", [0.0, 0.5, 1.0])
+def test_training_target_inverts_the_learned_warm_start(beta):
+    """The training target of a row is the network output that would make the oracle's
+    learned warm start land on the given multipliers.  A network whose output is the
+    constant c (all weights zero, output bias c) starts a substep from
+    beta lambda_prev + m g h^2 c; with no update applied (iteration cap 0) that start is
+    the substep's result, and the targets computed from it must be c on every existing
+    row, whatever the snake's mass, the substep length and beta."""
+    w = W.batched(n=5, seed=12, links=(1, 4))
+    w["mass"][:] = [0.01, 0.02, 0.005, 0.013, 0.01]
+    s = W.solver_settings(iters=10, n_sub=3)
+    o = oracle.OracleSim(w, s)
+    o.step(2)
+    c = 0.8125
+    p = np.zeros(M.N_PARAMS)
+    p[-1] = c
+    o.set_cfg(n_sub=1, iters=0, warm=2, beta=beta)
+    feat = o.features()
+    lam_prev = o.lam.copy()
+    o.step(1, mlp=p)
+    h = s["dt"] / 1
+    F, T = M.training_rows(o.node_off, w["mass"], feat, o.lam, lam_prev, beta, h)
+    n = len(W.n_nodes(w))
+    nodes = W.n_nodes(w)
+    # stretch (N - 1), yaw and pitch (2 (N - 2)), contact and friction (3 N) per snake
+    assert len(T) == int(sum(N - 1 + 2 * (N - 2) + 3 * N for N in nodes)) and n == 5
+    assert np.allclose(T, c, rtol=1e-12, atol=1e-12)
+    assert np.array_equal(F[:, :6].sum(1), np.ones(len(F)))

@@ -64,3 +64,24 @@ def test_noalloc_rejects_a_parameter_vector_it_cannot_hold():
                                  None)
     assert st == N.SIM_EINVAL
     assert b"exactly one" in lib.sim_last_error()
+
+
+def test_noalloc_and_handle_forward_reject_misaligned_features():
+    """The kernels read a feature row as four 16-byte vectors: a feature pointer off a
+    16-byte boundary is refused before anything is enqueued, by both entry points."""
+    from paper_1904_02833_gb300 import _native as N
+    from paper_1904_02833_gb300.mlp import WarmStartMLP, init_params
+
+    lib = N.load()
+    params = init_params(3)
+    p = torch.tensor(params, dtype=torch.float32, device="cuda")
+    f = torch.zeros(129 * 32 + 8, dtype=torch.bfloat16, device="cuda")
+    out = torch.zeros(128, device="cuda")
+    bad = ctypes.c_void_p(f.data_ptr() + 2 * 4)  # 8 bytes past an aligned base
+    st = lib.mlp_forward_noalloc(ctypes.c_void_p(p.data_ptr()), N.MLP_NUM_PARAMS, bad, 128,
+                                 ctypes.c_void_p(out.data_ptr()), None)
+    assert st == N.SIM_EINVAL and b"aligned" in lib.sim_last_error()
+    net = WarmStartMLP(params)
+    st = lib.mlp_forward(net.h, bad, 128, ctypes.c_void_p(out.data_ptr()))
+    assert st == N.SIM_EINVAL and b"aligned" in lib.sim_last_error()
+    net.close()
