@@ -41,34 +41,38 @@ namespace snakesim {
 constexpr unsigned kFull = 0xffffffffu;
 
 // atan(t) on [-1, 1]: odd polynomial t P(t^2) of degree 8 in t^2, a near-minimax fit
-// (iteratively reweighted least squares on Chebyshev nodes) made for this library; its
-// FP32 evaluation stays within ~1.1e-7 of atan (tests/test_fast_atan.py).  Beyond
-// |t| = 1, atan(t) = sign(t) pi/2 - atan(1/t).
+// (Lawson's iteratively reweighted least squares on Chebyshev nodes, tests/fit_atan.py
+// prints these float32 coefficients) made for this library; its FP32 evaluation stays
+// within ~1.1e-7 of atan (tests/test_fast_atan.py).  Beyond |t| = 1,
+// atan(t) = sign(t) pi/2 - atan(1/t).
 __device__ __forceinline__ float atan_unit(float t) {
   const float s = t * t;
-  float p = 2.456724454e-03f;
-  p = fmaf(p, s, -1.440136063e-02f);
-  p = fmaf(p, s, 3.978123527e-02f);
-  p = fmaf(p, s, -7.234859260e-02f);
-  p = fmaf(p, s, 1.049894763e-01f);
-  p = fmaf(p, s, -1.416122988e-01f);
-  p = fmaf(p, s, 1.998590693e-01f);
-  p = fmaf(p, s, -3.333259705e-01f);
-  p = fmaf(p, s, 9.999998864e-01f);
+  float p = 2.456725342e-03f;
+  p = fmaf(p, s, -1.440136135e-02f);
+  p = fmaf(p, s, 3.978123143e-02f);
+  p = fmaf(p, s, -7.234857976e-02f);
+  p = fmaf(p, s, 1.049894616e-01f);
+  p = fmaf(p, s, -1.416122913e-01f);
+  p = fmaf(p, s, 1.998590678e-01f);
+  p = fmaf(p, s, -3.333259821e-01f);
+  p = fmaf(p, s, 9.999998808e-01f);
   return t * p;
 }
 __device__ __forceinline__ float atan_any(float t) {
   const float a = fabsf(t);
-  if (a <= 1.f) return atan_unit(t);
-  return copysignf(1.57079632679489662f - atan_unit(__frcp_rn(a)), t);
+  const bool big = a > 1.f;
+  const float p = atan_unit(big ? __frcp_rn(a) : a);
+  return copysignf(big ? 1.57079632679489662f - p : p, t);
 }
-// atan2(y, x) for the bend angles from the same polynomial: x > 0 (|angle| < 90 degrees,
-// the normal case) directly, x < 0 shifted by +-pi, x = 0 at +-pi/2 (the library atan2f
-// would add a large body of code to every solver kernel for this rare branch).
+// atan2(y, x) for the bend angles from the same polynomial, without branches: atan(y / x),
+// shifted by +-pi for x < 0, +-pi/2 (0 for y = 0) on the axis x = 0.  (The library atan2f
+// would add a large body of code to every solver kernel for the rare angles beyond 90
+// degrees.)
 __device__ __forceinline__ float atan2_bend(float y, float x) {
-  if (x > 0.f) return atan_any(__fdividef(y, x));
-  if (x < 0.f) return atan_any(__fdividef(y, x)) + copysignf(3.14159265358979323846f, y);
-  return y > 0.f ? 1.57079632679489662f : (y < 0.f ? -1.57079632679489662f : 0.f);
+  float r = atan_any(__fdividef(y, x));
+  r = (x < 0.f) ? r + copysignf(3.14159265358979323846f, y) : r;
+  const float axis = (y == 0.f) ? 0.f : copysignf(1.57079632679489662f, y);
+  return (x == 0.f) ? axis : r;
 }
 
 struct Seg {  // derived quantities of the segment from node i to node i+1
@@ -125,19 +129,16 @@ __device__ __forceinline__ void friction_limit(const SnakeK& S, float bx, float 
     float a = px * bx + py * by, b = py * bx - px * by;
     const float u = a * S.inv_mu, v = b * S.inv_mu_side;
     const float r2 = u * u + v * v;
-    if (r2 > ln * ln) {
-      const float sc = ln > 0.f ? ln * rsqrtf(r2) : 0.f;
-      a *= sc; b *= sc;
-    }
+    const float sc = (r2 > ln * ln) ? (ln > 0.f ? ln * rsqrtf(r2) : 0.f) : 1.f;
+    a *= sc; b *= sc;
     px = a * bx - b * by;
     py = a * by + b * bx;
   } else {
+    // scale 1 inside the disc, rad / |p| outside, 0 for an empty disc; no branches
     const float rad = S.mu * ln;
     const float n2 = px * px + py * py;
-    if (n2 > rad * rad) {
-      if (rad > 0.f) { const float sc = rad * rsqrtf(n2); px *= sc; py *= sc; }
-      else { px = 0.f; py = 0.f; }
-    }
+    const float sc = (n2 > rad * rad) ? (rad > 0.f ? rad * rsqrtf(n2) : 0.f) : 1.f;
+    px *= sc; py *= sc;
   }
 }
 
@@ -149,11 +150,15 @@ namespace snakesim {
 
 // One pass over the rows at the current positions and multipliers.
 //   WARM = false: Jacobi pass.  Evaluates every row at (x^k, lambda^k), returns the
-//     group's normalised residual, and (unless `apply` comes back false) replaces
-//     lambda by its relaxed update and moves every free node by w_i sum_j grad_i c_j d_j.
+//     group's normalised residual, and (unless `stop` comes back true) replaces lambda by
+//     its relaxed update and moves every free node by w_i sum_j grad_i c_j d_j.
 //   WARM = true: warm-start pass.  Uses d_j = lambda_j (zeroing rows that do not exist
 //     or touch no free node) and applies it, so that M (x - x~) = J^T lambda.
-// `stop_at` returns the group's stop decision (residual <= tol or cap reached).
+// `stop` returns the group's stop decision (residual <= tol or cap reached).
+// The pass has no branches on row existence: every row of every node slot is evaluated
+// (on a straight dummy segment where the segment does not exist) and a row that does not
+// exist contributes d = 0 and residual 0, so that the lane's node slots form independent
+// instruction streams the scheduler can interleave.
 template <int NPL, int G, bool WARM, bool ANISO>
 __device__ __forceinline__ float row_pass(const SnakeK& S, const SolverArgs& A, int q,
                                           bool live, int kiter, const float (&xs)[NPL][3],
@@ -168,122 +173,112 @@ __device__ __forceinline__ float row_pass(const SnakeK& S, const SolverArgs& A, 
     dxl[d] = __shfl_up_sync(kFull, dx[NPL - 1][d], 1, G);
     dxr[d] = __shfl_down_sync(kFull, dx[0][d], 1, G);
   }
+  const int i0 = q * NPL;
+  // segment i (from node i to node i + 1) from its two end nodes; a straight dummy where
+  // the segment does not exist
+  auto seg = [&](int u) {
+    const int i = i0 + u - 1;
+    const bool on = live && i >= 0 && i + 1 <= S.N - 1;
+    const float* ax = (u == 0) ? xsl : xs[u > 0 ? u - 1 : 0];
+    const float* ad = (u == 0) ? dxl : dx[u > 0 ? u - 1 : 0];
+    const float* bx = (u == NPL) ? xsr : xs[u < NPL ? u : 0];
+    const float* bd = (u == NPL) ? dxr : dx[u < NPL ? u : 0];
+    const float ex = (bx[0] - ax[0]) + (bd[0] - ad[0]);
+    const float ey = (bx[1] - ax[1]) + (bd[1] - ad[1]);
+    const float ez = (bx[2] - ax[2]) + (bd[2] - ad[2]);
+    return make_seg(on ? ex : 1.f, on ? ey : 0.f, on ? ez : 0.f, L0);
+  };
   float acc[NPL][3];
   float dl[NPL][6];
   float accL[3] = {0.f, 0.f, 0.f}, accR[3] = {0.f, 0.f, 0.f};
 #pragma unroll
-  for (int j = 0; j < NPL; ++j) {
-    acc[j][0] = acc[j][1] = acc[j][2] = 0.f;
-#pragma unroll
-    for (int k = 0; k < 6; ++k) dl[j][k] = 0.f;
-  }
+  for (int j = 0; j < NPL; ++j) acc[j][0] = acc[j][1] = acc[j][2] = 0.f;
   float r = 0.f, q2 = 0.f;
-  const int i0 = q * NPL;
-  // segment i0-1 (from the left neighbour's last node to my first node)
-  Seg sp;
-  {
-    const bool ok = live && i0 >= 1 && i0 <= S.N - 1;
-    if (ok) sp = make_seg((xs[0][0] - xsl[0]) + (dx[0][0] - dxl[0]),
-                          (xs[0][1] - xsl[1]) + (dx[0][1] - dxl[1]),
-                          (xs[0][2] - xsl[2]) + (dx[0][2] - dxl[2]), L0);
-    else sp = make_seg(1.f, 0.f, 0.f, L0);
-  }
+  Seg sp = seg(0);  // segment i0 - 1
 #pragma unroll
   for (int j = 0; j < NPL; ++j) {
     const int i = i0 + j;
+    const Seg sc = seg(j + 1);  // segment i
     const bool act = live && i < S.N;
     const float wi = (i < S.nfix) ? 0.f : S.inv_m;
     const float wl = (i - 1 < S.nfix) ? 0.f : S.inv_m;
     const float wr = (i + 1 < S.nfix) ? 0.f : S.inv_m;
-    // segment i (my node j to node i+1)
-    float bsx, bsy, bsz, bdx, bdy, bdz;
-    if (j + 1 < NPL) {
-      bsx = xs[j + 1][0]; bsy = xs[j + 1][1]; bsz = xs[j + 1][2];
-      bdx = dx[j + 1][0]; bdy = dx[j + 1][1]; bdz = dx[j + 1][2];
-    } else {
-      bsx = xsr[0]; bsy = xsr[1]; bsz = xsr[2];
-      bdx = dxr[0]; bdy = dxr[1]; bdz = dxr[2];
-    }
-    const bool has_seg = act && i + 1 <= S.N - 1;
-    Seg sc = has_seg ? make_seg((bsx - xs[j][0]) + (bdx - dx[j][0]), (bsy - xs[j][1]) + (bdy - dx[j][1]),
-                                (bsz - xs[j][2]) + (bdz - dx[j][2]), L0)
-                     : make_seg(1.f, 0.f, 0.f, L0);
     float* tl = (j > 0) ? acc[j - 1] : accL;          // node i-1
     float* tr = (j + 1 < NPL) ? acc[j + 1] : accR;    // node i+1
     // ---- stretch (i, i+1): c = |e| - L0 (Eq. 3 with a constant rest length)
-    if (has_seg) {
+    {
       const float c = sc.len - L0;
       const float wg = wi + wr;
-      if (wg > 0.f) {
-        const float l = WARM ? 0.f : lam[j][0];
-        float d;
-        if (WARM) d = lam[j][0];
-        else {
-          r = fmaxf(r, fabsf(c + S.at_s * l) * S.inv_L0);
-          d = __fdividef(A.omega * (-c - S.at_s * l), wg + S.at_s);
-        }
-        dl[j][0] = d;
-        acc[j][0] -= sc.nx * d; acc[j][1] -= sc.ny * d; acc[j][2] -= sc.nz * d;
-        tr[0] += sc.nx * d; tr[1] += sc.ny * d; tr[2] += sc.nz * d;
+      const bool on = act && i + 1 <= S.N - 1 && wg > 0.f;
+      float d;
+      if (WARM) d = lam[j][0];
+      else {
+        const float l = lam[j][0];
+        r = fmaxf(r, on ? fabsf(c + S.at_s * l) * S.inv_L0 : 0.f);
+        d = __fdividef(A.omega * (-c - S.at_s * l), wg + S.at_s);
       }
+      d = on ? d : 0.f;
+      dl[j][0] = d;
+      acc[j][0] -= sc.nx * d; acc[j][1] -= sc.ny * d; acc[j][2] -= sc.nz * d;
+      tr[0] += sc.nx * d; tr[1] += sc.ny * d; tr[2] += sc.nz * d;
     }
     // ---- yaw and pitch bend centred on node i (rows in length units: L0 x angle)
-    if (act && i >= 1 && i <= S.N - 2) {
-      // yaw: L0 (atan2(z . (e1 x e2), e1_h . e2_h) - theta_rest)
-      {
-        const float cz = sp.ex * sc.ey - sp.ey * sc.ex;
-        const float dh = sp.ex * sc.ex + sp.ey * sc.ey;
-        const float c = L0 * (atan2_bend(cz, dh) - th[j]);
-        const float g0x = sp.gyx, g0y = sp.gyy;                   // node i-1
-        const float g1x = -sp.gyx - sc.gyx, g1y = -sp.gyy - sc.gyy; // node i
-        const float g2x = sc.gyx, g2y = sc.gyy;                   // node i+1
-        const float wg = wl * (g0x * g0x + g0y * g0y) + wi * (g1x * g1x + g1y * g1y) +
-                         wr * (g2x * g2x + g2y * g2y);
-        if (wg > 0.f) {
-          float d;
-          if (WARM) d = lam[j][1];
-          else {
-            const float l = lam[j][1];
-            r = fmaxf(r, fabsf(c + S.at_b * l) * S.inv_L0);
-            d = __fdividef(A.omega * (-c - S.at_b * l), wg + S.at_b);
-          }
-          dl[j][1] = d;
-          tl[0] += g0x * d; tl[1] += g0y * d;
-          acc[j][0] += g1x * d; acc[j][1] += g1y * d;
-          tr[0] += g2x * d; tr[1] += g2y * d;
-        }
+    const bool bend = act && i >= 1 && i <= S.N - 2;
+    // yaw: L0 (atan2(z . (e1 x e2), e1_h . e2_h) - theta_rest)
+    {
+      const float cz = sp.ex * sc.ey - sp.ey * sc.ex;
+      const float dh = sp.ex * sc.ex + sp.ey * sc.ey;
+      const float c = L0 * (atan2_bend(cz, dh) - th[j]);
+      const float g0x = sp.gyx, g0y = sp.gyy;                     // node i-1
+      const float g1x = -sp.gyx - sc.gyx, g1y = -sp.gyy - sc.gyy; // node i
+      const float g2x = sc.gyx, g2y = sc.gyy;                     // node i+1
+      const float wg = wl * (g0x * g0x + g0y * g0y) + wi * (g1x * g1x + g1y * g1y) +
+                       wr * (g2x * g2x + g2y * g2y);
+      const bool on = bend && wg > 0.f;
+      float d;
+      if (WARM) d = lam[j][1];
+      else {
+        const float l = lam[j][1];
+        r = fmaxf(r, on ? fabsf(c + S.at_b * l) * S.inv_L0 : 0.f);
+        d = __fdividef(A.omega * (-c - S.at_b * l), wg + S.at_b);
       }
-      // pitch: L0 (elevation(e2) - elevation(e1))
-      {
-        const float c = L0 * (sc.beta - sp.beta);
-        const float g0x = sp.gpx, g0y = sp.gpy, g0z = sp.gpz;
-        const float g1x = -sp.gpx - sc.gpx, g1y = -sp.gpy - sc.gpy, g1z = -sp.gpz - sc.gpz;
-        const float g2x = sc.gpx, g2y = sc.gpy, g2z = sc.gpz;
-        const float wg = wl * (g0x * g0x + g0y * g0y + g0z * g0z) +
-                         wi * (g1x * g1x + g1y * g1y + g1z * g1z) +
-                         wr * (g2x * g2x + g2y * g2y + g2z * g2z);
-        if (wg > 0.f) {
-          float d;
-          if (WARM) d = lam[j][2];
-          else {
-            const float l = lam[j][2];
-            r = fmaxf(r, fabsf(c + S.at_b * l) * S.inv_L0);
-            d = __fdividef(A.omega * (-c - S.at_b * l), wg + S.at_b);
-          }
-          dl[j][2] = d;
-          tl[0] += g0x * d; tl[1] += g0y * d; tl[2] += g0z * d;
-          acc[j][0] += g1x * d; acc[j][1] += g1y * d; acc[j][2] += g1z * d;
-          tr[0] += g2x * d; tr[1] += g2y * d; tr[2] += g2z * d;
-        }
+      d = on ? d : 0.f;
+      dl[j][1] = d;
+      tl[0] += g0x * d; tl[1] += g0y * d;
+      acc[j][0] += g1x * d; acc[j][1] += g1y * d;
+      tr[0] += g2x * d; tr[1] += g2y * d;
+    }
+    // pitch: L0 (elevation(e2) - elevation(e1))
+    {
+      const float c = L0 * (sc.beta - sp.beta);
+      const float g0x = sp.gpx, g0y = sp.gpy, g0z = sp.gpz;
+      const float g1x = -sp.gpx - sc.gpx, g1y = -sp.gpy - sc.gpy, g1z = -sp.gpz - sc.gpz;
+      const float g2x = sc.gpx, g2y = sc.gpy, g2z = sc.gpz;
+      const float wg = wl * (g0x * g0x + g0y * g0y + g0z * g0z) +
+                       wi * (g1x * g1x + g1y * g1y + g1z * g1z) +
+                       wr * (g2x * g2x + g2y * g2y + g2z * g2z);
+      const bool on = bend && wg > 0.f;
+      float d;
+      if (WARM) d = lam[j][2];
+      else {
+        const float l = lam[j][2];
+        r = fmaxf(r, on ? fabsf(c + S.at_b * l) * S.inv_L0 : 0.f);
+        d = __fdividef(A.omega * (-c - S.at_b * l), wg + S.at_b);
       }
+      d = on ? d : 0.f;
+      dl[j][2] = d;
+      tl[0] += g0x * d; tl[1] += g0y * d; tl[2] += g0z * d;
+      acc[j][0] += g1x * d; acc[j][1] += g1y * d; acc[j][2] += g1z * d;
+      tr[0] += g2x * d; tr[1] += g2y * d; tr[2] += g2z * d;
     }
     // ---- ground contact (Eq. 7, z - r >= 0) and Coulomb friction pair
-    if (act && A.contact && wi > 0.f) {
+    {
+      const bool on = act && A.contact && wi > 0.f;
       const float ln = lam[j][3];
       const float cn = (xs[j][2] - S.radius) + dx[j][2];
       const float ux = dx[j][0], uy = dx[j][1];
-      float dn, dx, dy;
-      if (WARM) { dn = ln; dx = lam[j][4]; dy = lam[j][5]; }
+      float dn, fx, fy;
+      if (WARM) { dn = ln; fx = lam[j][4]; fy = lam[j][5]; }
       else {
         // body tangent at the substep start (anisotropic friction only)
         float bx = 1.f, by = 0.f;
@@ -299,12 +294,12 @@ __device__ __forceinline__ float row_pass(const SnakeK& S, const SolverArgs& A, 
         }
         // residuals: Fischer-Burmeister on (c_n, w lambda_n); natural map of the cone
         const float b = wi * ln;
-        r = fmaxf(r, fabsf(cn + b - sqrtf(cn * cn + b * b)) * S.inv_L0);
+        r = fmaxf(r, on ? fabsf(cn + b - sqrtf(cn * cn + b * b)) * S.inv_L0 : 0.f);
         const float ax = wi * lam[j][4], ay = wi * lam[j][5];
         float px = ax - ux, py = ay - uy;
         friction_limit<ANISO>(S, bx, by, wi * ln, px, py);
         // squared friction residual; one square root per pass for the whole lane
-        q2 = fmaxf(q2, (ax - px) * (ax - px) + (ay - py) * (ay - py));
+        q2 = fmaxf(q2, on ? (ax - px) * (ax - px) + (ay - py) * (ay - py) : 0.f);
         // contact: lambda_n <- max(0, lambda_n + omega (-c_n / w))
         const float nl = fmaxf(0.f, ln - A.omega * cn * S.mass);
         dn = nl - ln;
@@ -313,12 +308,13 @@ __device__ __forceinline__ float row_pass(const SnakeK& S, const SolverArgs& A, 
         float tx = lam[j][4] - A.omega * ux * S.mass;
         float ty = lam[j][5] - A.omega * uy * S.mass;
         friction_limit<ANISO>(S, bx, by, ln, tx, ty);
-        dx = tx - lam[j][4]; dy = ty - lam[j][5];
+        fx = tx - lam[j][4]; fy = ty - lam[j][5];
       }
-      dl[j][3] = dn; dl[j][4] = dx; dl[j][5] = dy;
+      dn = on ? dn : 0.f; fx = on ? fx : 0.f; fy = on ? fy : 0.f;
+      dl[j][3] = dn; dl[j][4] = fx; dl[j][5] = fy;
       acc[j][2] += dn;
-      acc[j][0] += dx;
-      acc[j][1] += dy;
+      acc[j][0] += fx;
+      acc[j][1] += fy;
     }
     sp = sc;
   }
@@ -406,18 +402,13 @@ __device__ __forceinline__ void write_features(const SnakeK& S, const SolverArgs
       if (n2 > 0.f) { const float in = rsqrtf(n2); tx = ex * in; ty = ey * in; }
       else { tx = 1.f; ty = 0.f; }
     };
-    const bool has_next = i + 1 <= S.N - 1, has_prev = i >= 1;
-    const bool free_i = i >= S.nfix;
+    const bool has_next = i + 1 <= S.N - 1;
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
       float f[32];
 #pragma unroll
       for (int c = 0; c < 32; ++c) f[c] = 0.f;
-      bool ex;
-      if (k == 0) ex = has_next;
-      else if (k <= 2) ex = has_prev && has_next;
-      else ex = A.contact && free_i;
-      if (ex) {
+      if (feature_row_exists(i, k, S.N, S.nfix, A.contact)) {
         f[k] = 1.f;
         int na, nb = -1, nc = -1;  // local node indices 0..2 (i-1, i, i+1)
         float tx, ty;

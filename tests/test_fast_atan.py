@@ -59,3 +59,15 @@ def test_relative_accuracy_for_small_angles():
     c = coeffs()
     for t in np.geomspace(1e-7, 1e-2, 500):
         assert abs(float(atan_unit(t, c)) / math.atan(float(np.float32(t))) - 1) < 3e-7
+
+
+def test_coefficients_are_the_fit_script_output():
+    """tests/fit_atan.py regenerates the kernel's coefficients (float32, Horner order);
+    allow two float32 units of the last place for LAPACK rounding differences."""
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("fit_atan", os.path.join(os.path.dirname(__file__), "fit_atan.py"))
+    fa = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(fa)
+    mine = fa.horner_order(fa.fit())
+    for a, b in zip(mine, coeffs()):
+        assert abs(float(a) - float(b)) <= 2 * abs(float(np.spacing(np.float32(b)))), (a, b)
