@@ -7,9 +7,10 @@ batch state stays resident in HBM; L2 is flushed between timed steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
-Under torchrun every rank simulates its own batch (independent snakes, weak scaling);
-rank 0 prints one JSON line.  `--impl reference` times the FP64 CPU oracle instead on a
-bounded sample of the same workload.
+Under torchrun (N ranks) one seeded batch of N x 16384 snakes is split into N contiguous
+ranges balanced by node count (sim_partition), one per rank and GPU (independent snakes,
+no data-path collective, weak scaling); rank 0 prints one JSON line.  `--impl reference`
+times the FP64 CPU oracle instead on a bounded sample of the same workload.
 """
 from __future__ import annotations
 
@@ -51,10 +52,36 @@ BYTES_PER_LINK = 16
 BYTES_PER_SNAKE = 116
 
 
-def shard_seed(rank: int) -> int:
-    """Evaluation batch of a rank: rank 0 runs the evaluation seed 4, other ranks their own
-    seeds (independent snakes, weak scaling); all below the training seeds (1000+)."""
-    return 4 if rank == 0 else 100 + rank
+EVAL_SEED = 4  # the evaluation batch's seed, disjoint from the training seeds (1000+)
+
+
+def eval_batch(world: int) -> dict:
+    """The whole job's batch: N_SNAKES snakes per GPU drawn from one seed."""
+    return W.learned(n=N_SNAKES * world, seed=EVAL_SEED)
+
+
+def shard(w_all: dict, rank: int, world: int) -> dict:
+    """This rank's contiguous range of the batch (sim_partition: balanced by node count)."""
+    from paper_1904_02833_gb300.sim import partition
+    first = partition(w_all, world)
+    return W.subset(w_all, np.arange(first[rank], first[rank + 1]))
+
+
+def device_alu_peak(local: int):
+    """FP32 roof of the device: SMs x 128 FP32 lanes x 2 FLOP x the maximum SM clock, with
+    the SM count read from the device and the clock from nvidia-smi (else the measured
+    peaks file).  Returns (TFLOP/s, description)."""
+    import torch
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    mhz = None
+    try:
+        out = subprocess.run(["nvidia-smi", "-i", str(local), "--query-gpu=clocks.max.sm",
+                              "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=20)
+        mhz = float(out.stdout.strip().splitlines()[0])
+    except Exception:
+        mhz = peaks().get("sm_max_mhz")
+    mhz = float(mhz or 2070.0)
+    return sms * 128 * 2 * mhz * 1e6 / 1e12, "%d SMs x 128 FP32 lanes x 2 FLOP x %.0f MHz" % (sms, mhz)
 
 
 def aggregate(t_local: float, units_local: int, dist=None, device="cpu"):
@@ -161,10 +188,13 @@ def run_gpu(args):
         np.save(args.save_net, net.params())
     t_train = time.perf_counter() - t_train
 
-    w = W.learned(n=N_SNAKES, seed=shard_seed(rank))  # disjoint from the training seeds
+    w_all = eval_batch(world)  # disjoint from the training seeds
+    w = shard(w_all, rank, world)
+    n_local = len(w["n_links"])
     n_nodes_snake = w["n_links"] * w["seg_per_link"] + 1
     total_nodes = int(n_nodes_snake.sum())
     total_links = int(w["n_links"].sum())
+    alu_peak, alu_peak_source = device_alu_peak(local)
     sim = SnakeSim(w, W.solver_settings(iters=CAP, tol=TOL, warm=W_COLD))
     sim.set_mlp(net)
     stream = torch.cuda.current_stream()
@@ -179,8 +209,13 @@ def run_gpu(args):
              ("learned", dict(warm=2, beta=SKIP))]
     results = {}
     clk_all = None
+    layouts = {}
     for name, cfg in modes:
         sim.set_config(**cfg)
+        sim.snapshot_restore()
+        if not args.no_autotune:
+            sim.autotune(1)  # lane layouts per node count for this mode (untimed set-up)
+        layouts[name] = {int(N): "%dx%d" % sim.layout(int(N)) for N in np.unique(n_nodes_snake)}
         sim.snapshot_restore()
         sim.step(1, graph=True)  # capture / first replay, untimed
         sim.snapshot_restore()
@@ -207,7 +242,7 @@ def run_gpu(args):
             barrier()
         ms = [a.elapsed_time(b) for a, b in ev]
         t_local = sum(ms) / 1e3
-        value_all, t_max, _ = aggregate(t_local, N_SNAKES * args.steps, dist, "cuda")
+        value_all, t_max, _ = aggregate(t_local, n_local * args.steps, dist, "cuda")
         results[name] = dict(t=t_max, value=value_all, t_local=t_local, passes=passes, resid_max=resid_max,
                              unconverged=unconv, updates=upd, launches=sim.launches() - l0,
                              clocks=clk.summary())
@@ -231,28 +266,25 @@ def run_gpu(args):
     torch.cuda.synchronize()
     mlp_ms = float(np.median([a.elapsed_time(b) for a, b in evs]))
 
-    # end to end, learned mode, through the public API with the state in pinned host
-    # memory: the same K env-steps from the same start, state copied in and out each step
+    # end to end, learned mode, through the public C-ABI with the state in pinned host
+    # memory (is_device = 0: the library copies in and out): the same K env-steps from the
+    # same start, state copied in and out every step
     sim.set_config(warm=2, beta=SKIP)
     sim.snapshot_restore()
     start = sim.state()
-    start_lam = sim.lam()
-    host = {k: v.cpu().pin_memory() for k, v in start.items()}
-    host["lam"] = start_lam.cpu().pin_memory()
+    pin = lambda t: t.cpu().pin_memory()
+    host = {"pos": pin(start["pos"]), "vel": pin(start["vel"]), "press": pin(start["press"]),
+            "lam": pin(sim.lam()), "resid": pin(start["resid"]), "iters": pin(start["iters"])}
     inputs = ("pos", "vel", "press", "lam")
     barrier()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        dev = {k: host[k].to("cuda", non_blocking=True) for k in inputs}
-        sim.set_state(pos=dev["pos"], vel=dev["vel"], press=dev["press"], lam=dev["lam"])
+        sim.set_state_host(*(host[k] for k in inputs))
         sim.step(1, graph=True)
-        d = sim.state()
-        d["lam"] = sim.lam()
-        for k in host:
-            host[k].copy_(d[k], non_blocking=True)
+        sim.get_state_host(host["pos"], host["vel"], host["press"], host["lam"], host["resid"], host["iters"])
     torch.cuda.synchronize()
     t_e2e = time.perf_counter() - t0
-    e2e_value, _, _ = aggregate(t_e2e, N_SNAKES * args.steps, dist, "cuda")
+    e2e_value, _, _ = aggregate(t_e2e, n_local * args.steps, dist, "cuda")
     h2d = int(sum(host[k].numel() * host[k].element_size() for k in inputs))
     d2h = int(sum(v.numel() * v.element_size() for v in host.values()))
 
@@ -277,14 +309,15 @@ def run_gpu(args):
 
     solvers = None if args.no_solver_comparison else solver_comparison(args, flush, stream, local)
     calib = None if args.no_calibration else calibration_leg(stream)
-    fem = None if args.no_fem else fem_link_leg(flush, stream)
+    fem = None if args.no_fem else fem_link_leg(flush, stream, alu_peak)
+    single = None if args.no_configs else single_snake_leg(stream)
+    fixed = None if args.no_configs else fixed_iterations_leg(flush, stream, alu_peak)
 
     if rank == 0:
         pk = peaks()
         L = results["learned"]
         value = L["value"]
-        alu_peak = 152 * 128 * 2 * 2070.0 * 1e6 / 1e12
-        alu_measured = fp32_peak_measured(stream)
+        alu_measured = fp32_peak_measured(stream, local)
         # solver family in the learned mode: Jacobi passes per step x 216 FLOP / time
         # (the network's share of the step is taken out with its own measured time)
         solver_time = L["t_local"] / args.steps - 20 * mlp_ms / 1e3
@@ -300,7 +333,7 @@ def run_gpu(args):
                                     "tflops": kflop.get(k, 0.0) / (v[0] / 1e3) / 1e12}
                       for k, v in sorted(ktimes.items())}
         bytes_step = (BYTES_PER_NODE * total_nodes + BYTES_PER_LINK * total_links
-                      + BYTES_PER_SNAKE * N_SNAKES)
+                      + BYTES_PER_SNAKE * n_local)
         mlp_flop_row = 2 * (24 * 128 + 128 * 128 + 128)
         mlp_tflops = mlp_flop_row * rows / (mlp_ms / 1e3) / 1e12
         bf16_peak = pk.get("bf16_tflops", 1900.0)
@@ -311,7 +344,7 @@ def run_gpu(args):
                 "value": R["value"], "ms_per_step": R["t"] * 1e3 / args.steps,
                 "updates_per_substep_by_step": [round(u, 2) for u in R["updates"]],
                 "residual_max": R["resid_max"], "unconverged_snake_steps": R["unconverged"],
-                "gpu_launches": R["launches"], "clocks": R["clocks"]}
+                "gpu_launches": R["launches"], "clocks": R["clocks"], "layouts": layouts[name]}
         res = {
             "metric": METRIC,
             "value": value,
@@ -329,9 +362,11 @@ def run_gpu(args):
             "plain_value": modes_out["plain"]["value"],
             "learned_vs_plain": value / modes_out["plain"]["value"],
             "modes": modes_out,
-            "config": dict(workload_config(total_nodes, world),
-                           l2="flushed between timed steps (256 MB write)",
-                           training={"seconds": round(t_train, 1), "rounds": record}),
+            "config": workload_config(int(W.n_nodes(w_all).sum()), world),
+            "l2": "flushed between timed steps (256 MB write)",
+            "training": {"seconds": round(t_train, 1), "rounds": record},
+            "shard": {"rank": rank, "snakes": n_local, "nodes": total_nodes,
+                      "rule": "contiguous snake ranges of one seeded batch, balanced by node count"},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
                          "frac": achieved / alu_peak, "traffic": traffic,
                          "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one "
@@ -344,7 +379,7 @@ def run_gpu(args):
                                            "note": "all layout kernels of the learned step, step time "
                                                    "minus the network's"},
                          "per_layout": per_layout,
-                         "peak_source": "152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz",
+                         "peak_source": alu_peak_source,
                          "peak_measured": alu_measured,
                          "frac_of_measured": achieved / alu_measured,
                          "peak_measured_source": "sim_fp32_fma_probe: 1216 x 256 threads, 8 independent "
@@ -367,12 +402,19 @@ def run_gpu(args):
             res["solver_comparison"] = solvers
         if calib is not None:
             res["calibration"] = calib
+        if single is not None:
+            res["single_snake"] = single
+        if fixed is not None:
+            fixed["roofline"]["peak_measured"] = alu_measured
+            fixed["roofline"]["frac_of_measured"] = fixed["roofline"]["achieved"] / alu_measured
+            res["fixed_iterations"] = fixed
         if fem is not None:
             fem["roofline"]["peak_measured"] = alu_measured
             fem["roofline"]["frac_of_measured"] = fem["roofline"]["achieved"] / alu_measured
             res["fem_link"] = fem
         if world == 1 and not args.no_cpu_baseline:
             res["cpu_baseline"] = cpu_baseline(w, W.solver_settings(iters=CAP, tol=TOL, warm=W_COLD))
+            res["cpu_baseline"]["sample"] += " (the workload's snakes, FP64 oracle)"
         print(json.dumps(res), flush=True)
     sim.close()
     net.close()
@@ -434,13 +476,14 @@ FEM_FLOP_PER_ELEMENT_SUBSTEP = 2 * 500 + 130
 FEM_DRAM_BYTES_PER_LINK = 6.701568e6 / 1216
 
 
-def fp32_peak_measured(stream, n_blocks=152 * 8, iters=20000):
-    """The library's FMA probe (8 independent chains per thread, full occupancy), best of
-    three timed launches: the measured FP32 roof beside the derived one."""
+def fp32_peak_measured(stream, local=0, iters=20000):
+    """The library's FMA probe (8 independent chains per thread, 8 blocks of 256 threads per
+    SM), best of three timed launches: the measured FP32 roof beside the derived one."""
     import ctypes
     import torch
     from paper_1904_02833_gb300 import _native as N
     L = N.load()
+    n_blocks = 8 * torch.cuda.get_device_properties(local).multi_processor_count
     out = torch.empty(n_blocks * 256, dtype=torch.float32, device="cuda")
     args = (ctypes.c_void_p(out.data_ptr()), n_blocks, iters, ctypes.c_void_p(stream.cuda_stream))
     N.check(L.sim_fp32_fma_probe(*args))
@@ -457,7 +500,7 @@ def fp32_peak_measured(stream, n_blocks=152 * 8, iters=20000):
     return n_blocks * 256 * iters * 256 / (best / 1e3) / 1e12
 
 
-def fem_link_leg(flush, stream, n=1216, frames=10, warmup=3):
+def fem_link_leg(flush, stream, alu_peak, n=1216, frames=10, warmup=3):
     """The tetrahedral soft link (Sec. III-B; the paper's frame: 2 substeps, 20 PCR
     iterations each): a batch of 1216 links (8 per SM) on the 13-cross-section mesh, one
     thread block per link, timed per frame with CUDA events, L2 flushed between frames;
@@ -484,7 +527,6 @@ def fem_link_leg(flush, stream, n=1216, frames=10, warmup=3):
     NT = len(M["tets"])
     flop = NT * (FEM_FLOP_PER_ELEMENT_PRODUCT * float(mv.astype(np.float64).sum())
                  + FEM_FLOP_PER_ELEMENT_SUBSTEP * s["n_sub"] * n)
-    alu_peak = 152 * 128 * 2 * 2070.0 * 1e6 / 1e12
     achieved = flop / (t / 1e3) / 1e12
     cores = os.cpu_count() or 1
     sample = W.fem_links(n, seed=6)
@@ -511,6 +553,89 @@ def fem_link_leg(flush, stream, n=1216, frames=10, warmup=3):
     return out
 
 
+# Jacobi passes per substep at a fixed budget of K updates: K applied passes and the final
+# evaluation pass (the residual at the last iterate is measured, its update not applied).
+def passes_fixed(K):
+    return K + 1
+
+
+def single_snake_leg(stream, steps=600, calls=120):
+    """The paper's real-time setting (the one-snake configuration): one 4-link snake of 41
+    nodes, env-steps of 1/60 s with 20 substeps of exactly 10 Jacobi updates.  Timed with
+    CUDA events two ways: 600 env-steps in one call (the persistent kernel runs them all),
+    and one call per env-step (a captured one-step graph, the way a 60 Hz control loop
+    would step it), against the real-time budget of 1/60 s per env-step (Sec. VI)."""
+    import torch
+    from paper_1904_02833_gb300.sim import SnakeSim
+    w = W.single_snake()
+    sim = SnakeSim(w, W.solver_settings(iters=10))
+    sim.step(3)
+    sim.step(1, graph=True)  # capture, untimed
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    sim.step(steps)
+    b.record(stream)
+    b.synchronize()
+    batched = a.elapsed_time(b) / steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(calls)]
+    for e0, e1 in ev:
+        e0.record(stream)
+        sim.step(1, graph=True)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    per = np.array([e0.elapsed_time(e1) for e0, e1 in ev])
+    st = sim.state_host()
+    sim.close()
+    budget = 1000.0 / 60.0
+    return {"workload": "1 snake x 41 nodes (4 links x 10 segments), 20 substeps x 10 Jacobi updates, "
+                        "%d env-steps in one call; %d calls of one env-step" % (steps, calls),
+            "ms_per_env_step_batched": batched,
+            "ms_per_env_step_per_call": {"median": float(np.median(per)), "p99": float(np.percentile(per, 99)),
+                                         "max": float(per.max())},
+            "realtime_budget_ms": budget, "realtime_factor_per_call": budget / float(np.median(per)),
+            "updates_per_substep": float(st["iters"][0]) / 20, "finite": bool(np.isfinite(st["pos"]).all()),
+            "paper_context": "Table II: one snake, 1/60 s frames, real time on a GTX 1080 Ti"}
+
+
+def fixed_iterations_leg(flush, stream, alu_peak, n=4096, steps=600, K=10):
+    """Batched locomotion at a fixed budget (the 4096-snake configuration): uneven snakes of
+    2-8 links, 20 substeps of exactly 10 Jacobi updates, 600 env-steps, lane layouts chosen
+    by sim_autotune, the 600 env-steps replayed as one captured CUDA graph (one persistent
+    kernel per layout).  env-steps/s, and the ALU roofline of the whole replay (every
+    snake runs the same passes, so no tail of slow snakes)."""
+    import torch
+    from paper_1904_02833_gb300.sim import SnakeSim
+    w = W.batched(n=n, seed=3)
+    sim = SnakeSim(w, W.solver_settings(iters=K))
+    sim.step(3)
+    sim.autotune(1)
+    sim.snapshot_save()
+    sim.step(steps, graph=True)  # capture and first replay, untimed
+    sim.snapshot_restore()
+    flush.zero_()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    sim.step(steps, graph=True)
+    b.record(stream)
+    b.synchronize()
+    t = a.elapsed_time(b) / 1e3
+    st = sim.state_host()
+    layouts = {int(N): "%dx%d" % sim.layout(int(N)) for N in np.unique(W.n_nodes(w))}
+    sim.close()
+    nodes = int(W.n_nodes(w).sum())
+    flop = FLOP_PER_NODE_PASS * passes_fixed(K) * 20 * nodes * steps
+    achieved = flop / t / 1e12
+    return {"workload": "%d uneven snakes (2-8 links x 10 segments, %d nodes), 20 substeps x %d Jacobi updates, "
+                        "%d env-steps in one graph replay, autotuned layouts" % (n, nodes, K, steps),
+            "env_steps_per_s": n * steps / t, "ms_per_env_step": t * 1e3 / steps,
+            "layouts": layouts, "updates_per_substep": float(st["iters"].mean()) / 20,
+            "finite": bool(np.isfinite(st["pos"]).all()),
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+                         "frac": achieved / alu_peak,
+                         "flop_model": "216 FLOP per node and pass x 11 passes per substep (10 updates + the "
+                                       "final evaluation) x 20 substeps x nodes x env-steps"}}
+
+
 def calibration_leg(stream, n=1024, steps=200, ckpt=20):
     """The differentiable calibration rollout: 1024 four-link snakes, 200 env-steps of 20
     substeps with 10 Jacobi updates each, checkpoints every 20 env-steps; the forward
@@ -529,7 +654,7 @@ def calibration_leg(stream, n=1024, steps=200, ckpt=20):
     sim.step(1)
     sim.snapshot_save()
     th = theta_of(guess).cuda().requires_grad_(True)
-    rollout(sim, th, 2, ckpt).sum().backward()  # warm-up (allocations, first launches)
+    rollout(sim, th, steps, ckpt).sum().backward()  # full-length warm-up (buffers sized, first launches)
     sim.snapshot_restore()
     th.grad = None
     e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
@@ -583,11 +708,12 @@ def cpu_baseline(w, s, n_sample=None, budget_s=20.0):
 
 
 def workload_config(total_nodes, world):
-    """The benchmark's workload, the same in both arms."""
-    return {"workload": "%d uneven snakes (2-8 links x 10 segments, %d nodes), dt 1/60 s,"
-                        " 20 substeps, Jacobi to residual %g (cap %d updates/substep)"
-                        % (N_SNAKES, total_nodes, TOL, CAP),
-            "snakes_per_gpu": N_SNAKES, "nodes_per_gpu": total_nodes,
+    """The benchmark's workload, the same dict in both arms (total_nodes: the whole job's
+    batch of N_SNAKES x world snakes)."""
+    return {"workload": "%d uneven snakes per GPU (2-8 links x 10 segments), dt 1/60 s, 20 substeps, Jacobi"
+                        " to residual %g (cap %d updates/substep); %d GPU(s), one seeded batch split into"
+                        " contiguous node-balanced ranges" % (N_SNAKES, TOL, CAP, world),
+            "snakes_per_gpu": N_SNAKES, "nodes_per_gpu": round(total_nodes / world, 1),
             "parallelism": "independent snakes per GPU (dp%d)" % world}
 
 
@@ -596,13 +722,13 @@ def run_reference(args):
     if rank != 0:
         return
     import oracle
-    w = W.learned(n=N_SNAKES, seed=4)
+    w_all = eval_batch(world)
     s = W.solver_settings(iters=CAP, tol=TOL, warm=W_COLD)
     cores = os.cpu_count() or 1
     rng = np.random.default_rng(7)
     n_sample = cores
-    sel = np.sort(rng.choice(N_SNAKES, n_sample, replace=False))
-    o = oracle.OracleSim(W.subset(w, sel), s, n_threads=cores)
+    sel = np.sort(rng.choice(len(w_all["n_links"]), n_sample, replace=False))
+    o = oracle.OracleSim(W.subset(w_all, sel), s, n_threads=cores)
     for _ in range(args.warmup):
         o.step(1)
     t0 = time.perf_counter()
@@ -610,14 +736,15 @@ def run_reference(args):
         o.step(1)
     dt = time.perf_counter() - t0
     value = n_sample * args.steps / dt
-    sample = ("%d snakes drawn from the %d-snake batch, %d env-steps per step (FP64 oracle, OpenMP)"
-              % (n_sample, N_SNAKES, 1))
+    sample = ("%d snakes drawn from the %d-snake batch, 1 env-step per timed step (FP64 oracle, OpenMP)"
+              % (n_sample, len(w_all["n_links"])))
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": "env-steps/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": workload_config(int(W.n_nodes(w).sum()), world),
+        "config": workload_config(int(W.n_nodes(w_all).sum()), world),
+        "reference_sample": sample,
         "cpu_baseline": {"value": value, "unit": "env-steps/s", "cores": cores, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": "env-steps/s", "h2d_bytes_per_step": 0,
@@ -639,6 +766,10 @@ def main():
                     help="skip the differentiable calibration leg (forward + adjoint)")
     ap.add_argument("--no-fem", action="store_true",
                     help="skip the tetrahedral soft-link leg")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default lane layouts instead of timing them per mode (sim_autotune)")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the single-snake and fixed-iteration (4096 snakes) legs")
     ap.add_argument("--save-net", default=None, help="write the trained network parameters (.npy)")
     ap.add_argument("--load-net", default=None, help="use saved network parameters instead of training")
     ap.add_argument("--snakes", type=int, default=N_SNAKES,

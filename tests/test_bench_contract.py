@@ -23,6 +23,13 @@ def test_reference_arm_prints_one_contract_line():
     assert d["metric"].startswith("snake env-steps/s")
     assert d["config"]["snakes_per_gpu"] == 16384 and d["config"]["nodes_per_gpu"] > 16384 * 20
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["cpu_baseline"]["kind"] == "oracle"
+    # the GPU arm builds its config with the same function on the same batch: equal dicts,
+    # the reference arm's sample stated under its own key
+    sys.path.insert(0, ROOT)
+    import bench
+    import workloads as W
+    assert d["config"] == bench.workload_config(int(W.n_nodes(bench.eval_batch(1)).sum()), 1)
+    assert "sample" not in d["config"] and "snakes" in d["reference_sample"]
 
 
 def test_cpu_baseline_reports_all_cores_and_one_core():
