@@ -1,12 +1,21 @@
 """Parity of the CUDA path (through the C-ABI) with the FP64 oracle on the same seeded
 inputs, element by element.
 
-Tolerances (FP32 kernel against FP64 oracle):
-  * positions after one env-step: 1e-5 relative to the largest coordinate;
-  * velocities: v = d / h with d the last substep's displacement, so the position
-    differences of the substep (observed ~1e-7..1e-6 m once friction cone projections,
-    a non-smooth branch, pass rounding differences on) arrive divided by h = 1/1200 s;
-    bound 1.2e-3 m/s (1e-6 m / h);
+Tolerances (FP32 kernel against FP64 oracle), per node, with s_i the node's length scale
+(the larger of its distance from the origin and its snake's rest length):
+  * positions after one env-step: |x_gpu - x_oracle| <= 1e-5 s_i (the one-step relative
+    figure the method is held to); observed up to 1.8e-6 s_i;
+  * velocities: v = d / h with d the last substep's displacement (a difference of two
+    positions that agree to many digits), so its FP32 error is set by the rounding of the
+    positions rather than by |v|: the positions at every substep boundary are stored in
+    FP32, each rounded by up to 2^-24 s_i, and the last substep's displacement inherits
+    the geometry those roundings leave; bound n_sub 2^-24 s_i / h (1.43e-3 s_i m/s at
+    dt = 1/60 s, 20 substeps); observed up to 3.3e-4 m/s on the Jacobi cases, 1.2e-3 on
+    falling snakes after 63 Newton + PCR products;
+  * two documented floors above that: 5e-3 m/s where the solve stops at a tolerance and
+    FP32 and FP64 may stop a substep one Newton step apart, and where the bfloat16
+    network sets the start of an unconverged solve (its outputs agree to ~5e-3 of
+    their scale);
   * chamber pressures: FP32 rounding of the decay factor, the gait sine and the
     parameters (~6e-8 relative each) accumulates over the substeps; bound 1e-5;
   * multipliers after a fixed number of updates (an unconverged iterate, where the
@@ -69,11 +78,15 @@ def node_scale(w, x):
     return np.maximum(np.linalg.norm(x, axis=1), ell)
 
 
-def compare(gpu, ref, pos_rel=1e-5, vel_abs=1.2e-3):
-    """Per node: |x_gpu - x_oracle| <= pos_rel x node_scale, |v_gpu - v_oracle| <= vel_abs;
-    chamber pressures to 1e-5.  Records the per-element statistics."""
+def compare(gpu, ref, pos_rel=1e-5, vel_floor=0.0):
+    """Per node: |x_gpu - x_oracle| <= pos_rel s_i and
+    |v_gpu - v_oracle| <= max(n_sub 2^-24 s_i / h, vel_floor); chamber pressures to 1e-5.
+    Records the per-element statistics."""
     st = gpu.state_host()
     scale = node_scale(ref.w, ref.x)
+    n_sub = ref.s["n_sub"]
+    h = ref.s["dt"] / n_sub
+    vel_bound = np.maximum(n_sub * 2.0 ** -24 * scale / h, vel_floor)
     ep = np.linalg.norm(st["pos"] - ref.x, axis=1) / scale
     ev = np.linalg.norm(st["vel"] - ref.v, axis=1)
     vref = np.linalg.norm(ref.v, axis=1)
@@ -82,10 +95,10 @@ def compare(gpu, ref, pos_rel=1e-5, vel_abs=1.2e-3):
                   "pos_rel_max": float(ep.max()), "pos_rel_p99": float(np.percentile(ep, 99)),
                   "vel_abs_max": float(ev.max()), "vel_abs_p99": float(np.percentile(ev, 99)),
                   "vel_abs_median": float(np.median(ev)), "speed_median": float(np.median(vref)),
-                  "vel_rel_p99": float(np.percentile(ev / np.maximum(vref, 1e-3), 99)),
-                  "press_abs_max": float(epr), "bounds": [pos_rel, vel_abs]})
+                  "vel_over_bound_max": float((ev / vel_bound).max()),
+                  "press_abs_max": float(epr), "bounds": [pos_rel, vel_floor]})
     assert ep.max() <= pos_rel, (ep.max(), int(ep.argmax()))
-    assert ev.max() <= vel_abs, (ev.max(), int(ev.argmax()))
+    assert (ev <= vel_bound).all(), ((ev / vel_bound).max(), int((ev / vel_bound).argmax()))
     assert epr <= 1e-5, epr
     return st
 
@@ -300,7 +313,7 @@ def test_newton_pcr_matches_oracle(tol, iters):
         o.step(1)
         # to a tolerance, FP32 and FP64 may stop a substep one Newton step apart; where x
         # ends depends on the path by a second-order term (~1e-6 m here), i.e. ~1e-3 m/s
-        compare(g, o, vel_abs=1.2e-3 if tol == 0.0 else 5e-3)
+        compare(g, o, vel_floor=0.0 if tol == 0.0 else 5e-3)
     st = g.state_host()
     if tol == 0.0:
         assert (st["iters"] == 20 * 63).all() and (o.iters == 20 * 63).all()
@@ -330,7 +343,7 @@ def test_newton_pcr_with_learned_warm_start_matches_oracle():
     # the network's outputs agree to ~5e-3 of their scale (bfloat16 operands, hardware
     # tanh); after two Newton steps the end state still depends on that start, and the
     # velocity is the substep displacement over h
-    compare(g, o, vel_abs=5e-3)
+    compare(g, o, vel_floor=5e-3)
 
 
 def test_autotune_keeps_the_state_and_the_physics():
