@@ -33,6 +33,12 @@ N_SNAKES = 16384
 TOL = 1e-4
 CAP = 5000
 SKIP = 0.5  # learned warm start: lambda0 = SKIP lambda_prev + m g h^2 network(features)
+# the learned warm start the metric is quoted on: the network at every substep, on every
+# row kind; and the variants timed beside it
+LEARNED = dict(net_rows=0, net_every=1)
+TARGET_WARM = 0  # training targets: solves from zero multipliers
+LEARNED_VARIANTS = {"bilateral": dict(net_rows=1, net_every=1), "every2": dict(net_rows=0, net_every=2),
+                    "every4": dict(net_rows=0, net_every=4), "bilateral_every2": dict(net_rows=1, net_every=2)}
 # Algorithmic FP32 operations of one Jacobi pass per node (segment geometry 29, stretch
 # 23, yaw 46, pitch 52, contact + friction 54, update 12; a division, square root or
 # transcendental counts as one operation).
@@ -183,7 +189,7 @@ def run_gpu(args):
         from paper_1904_02833_gb300.mlp import WarmStartMLP
         net, record = WarmStartMLP(np.load(args.load_net)), [{"loaded": args.load_net}]
     else:
-        net, record = train_warm_start(n_snakes=2048, rounds=2, skip=SKIP)
+        net, record = train_warm_start(n_snakes=2048, rounds=2, skip=SKIP, target_warm=args.target_warm)
     if args.save_net:
         np.save(args.save_net, net.params())
     t_train = time.perf_counter() - t_train
@@ -206,7 +212,10 @@ def run_gpu(args):
     sim.snapshot_save()
 
     modes = [("plain", dict(warm=0, beta=1.0)), ("previous", dict(warm=1, beta=0.5)),
-             ("learned", dict(warm=2, beta=SKIP))]
+             ("learned", dict(warm=2, beta=SKIP, **LEARNED))]
+    if not args.no_learned_variants:
+        # the network on the bilateral rows only, and every second / fourth substep only
+        modes += [("learned_" + k, dict(warm=2, beta=SKIP, **v)) for k, v in LEARNED_VARIANTS.items()]
     results = {}
     clk_all = None
     layouts = {}
@@ -227,6 +236,7 @@ def run_gpu(args):
         clk = Clocks(local)
         with clk:
             barrier()
+            torch.cuda.nvtx.range_push("timed_" + name)  # lets a profiler take the timed steps alone
             for k in range(args.steps):
                 flush.zero_()  # L2 (129 MB) flush between timed steps, outside the events
                 ev[k][0].record(stream)
@@ -239,6 +249,7 @@ def run_gpu(args):
                 upd.append(float(its.mean()) / 20)
                 resid_max = max(resid_max, float(st["resid"].max()))
                 unconv += int((st["resid"] > TOL).sum())
+            torch.cuda.nvtx.range_pop()
             barrier()
         ms = [a.elapsed_time(b) for a, b in ev]
         t_local = sum(ms) / 1e3
@@ -269,7 +280,7 @@ def run_gpu(args):
     # end to end, learned mode, through the public C-ABI with the state in pinned host
     # memory (is_device = 0: the library copies in and out): the same K env-steps from the
     # same start, state copied in and out every step
-    sim.set_config(warm=2, beta=SKIP)
+    sim.set_config(warm=2, beta=SKIP, **LEARNED)
     sim.snapshot_restore()
     start = sim.state()
     pin = lambda t: t.cpu().pin_memory()
@@ -291,7 +302,7 @@ def run_gpu(args):
     # per-layout kernel times of the learned step (direct launches with an event pair
     # around every solver kernel, on the stream it is launched on), for the roofline of
     # the dominant kernel
-    sim.set_config(warm=2, beta=SKIP)
+    sim.set_config(warm=2, beta=SKIP, **LEARNED)
     sim.snapshot_restore()
     sim.step(1)
     sim.kernel_times()
@@ -766,6 +777,11 @@ def main():
                     help="skip the differentiable calibration leg (forward + adjoint)")
     ap.add_argument("--no-fem", action="store_true",
                     help="skip the tetrahedral soft-link leg")
+    ap.add_argument("--target-warm", type=int, default=TARGET_WARM, choices=[0, 1],
+                    help="start of the solves that make the network's training targets: 0 cold, "
+                         "1 beta x the previous multipliers")
+    ap.add_argument("--no-learned-variants", action="store_true",
+                    help="time only the headline learned configuration (not its variants)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default lane layouts instead of timing them per mode (sim_autotune)")
     ap.add_argument("--no-configs", action="store_true",

@@ -89,7 +89,17 @@ typedef struct {
   int32_t solver;     /* SIM_SOLVER_*                                                    */
   int32_t pcr_iters;  /* SIM_SOLVER_NEWTON_PCR: PCR iterations per Newton step (>= 1; the *
                        * paper uses 20)                                                   */
+  /* SIM_WARM_LEARNED only:                                                               */
+  int32_t net_rows;   /* SIM_NET_ROWS_*: the row kinds the network predicts               */
+  int32_t net_every;  /* the network runs at substeps s with s % net_every == 0 (0 is     *
+                       * read as 1); the substeps in between start from beta lambda_prev  *
+                       * and run in the same launch as the network substep before them   */
 } SimConfig;
+
+/* Row kinds the network predicts in the learned warm start: all six (stretch, yaw, pitch,
+ * contact, friction x / y), or the bilateral rows only (stretch, yaw, pitch), the
+ * contact and friction rows then starting from beta lambda_prev. */
+enum { SIM_NET_ROWS_ALL = 0, SIM_NET_ROWS_BILATERAL = 1 };
 
 /* Substep solvers: the Jacobi relaxation of Eq. 8 (`iters` caps its updates), or the
  * paper's Newton steps with a preconditioned conjugate residual solve of the Schur system

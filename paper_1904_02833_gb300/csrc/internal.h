@@ -71,6 +71,10 @@ struct SolverArgs {
   int law_every;          // SIM_LATENCY_LAW: substeps per law step
   float k_i, k_d, t_p, p_s;
   int pcr_iters;          // SIM_SOLVER_NEWTON_PCR: PCR iterations per Newton step
+  int net_rows;           // SIM_WARM_LEARNED: SIM_NET_ROWS_*
+  int net_every;          // SIM_WARM_LEARNED: the network's substeps are multiples of it (>= 1)
+  int span;               // split mode: substeps the launch finishes (the first one with the
+                          // network's start, the others from beta lambda_prev)
 };
 
 // Calibration (adjoint) state of a simulator, defined in adjoint.cu.
@@ -88,7 +92,9 @@ SimStatus calib_backward(CalibState& C, const SnakeParams* prm, const int* node_
 // Records the message returned by sim_last_error() on this thread.
 void set_last_error(const char* msg);
 // Enqueues the warm-start network on `feat` [rows][32] -> out [rows] (no synchronisation).
+// bilateral = 1: only the first three of every six rows (stretch, yaw, pitch of a node);
+// rows then counts those rows.
 SimStatus mlp_forward_launch(MlpHandle* h, const void* feat, long long rows, float* out,
-                             cudaStream_t stream);
+                             cudaStream_t stream, int bilateral);
 
 }  // namespace snakesim

@@ -138,9 +138,15 @@ constexpr int kInferThreads = 256;
 // 32 (w % 4) .. +31) and takes the column half w / 4 of both epilogues, so each row's
 // 256 SiLU evaluations are split between two threads; the next tile's features are
 // loaded into registers while the current tile's MMAs run.
+// bilateral = 1: the network's row r is row 6 (r / 3) + r % 3 of feat and out (the stretch,
+// yaw and pitch rows of node r / 3 in the solver's six-rows-per-node order).
+__device__ __forceinline__ long long infer_row(long long r, int bilateral) {
+  return bilateral ? 6 * (r / 3) + r % 3 : r;
+}
 __global__ void __launch_bounds__(kInferThreads, 2) mlp_infer_kernel(const __nv_bfloat16* __restrict__ feat,
                                                                     long long rows, MlpDev w,
-                                                                    float* __restrict__ out, int* err) {
+                                                                    float* __restrict__ out, int* err,
+                                                                    int bilateral) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   InferSmem& S = *reinterpret_cast<InferSmem*>(smem_raw);
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
@@ -172,7 +178,7 @@ __global__ void __launch_bounds__(kInferThreads, 2) mlp_infer_kernel(const __nv_
       const int c = t + u * kInferThreads;
       const long long r = tile * kTile + (c >> 2);
       v[u] = make_uint4(0u, 0u, 0u, 0u);
-      if (tile < ntiles && r < rows) v[u] = reinterpret_cast<const uint4*>(feat + r * kInPad)[c & 3];
+      if (tile < ntiles && r < rows) v[u] = reinterpret_cast<const uint4*>(feat + infer_row(r, bilateral) * kInPad)[c & 3];
     }
   };
   uint4 nxt[2];
@@ -242,7 +248,7 @@ __global__ void __launch_bounds__(kInferThreads, 2) mlp_infer_kernel(const __nv_
     __syncthreads();
     tc::fence_after_sync();
     const long long r = tile * kTile + row;
-    if (half == 0 && r < rows) out[r] = (y + S.part[row]) + b3;
+    if (half == 0 && r < rows) out[infer_row(r, bilateral)] = (y + S.part[row]) + b3;
   }
   if (!ok) {
     if (t == 0) atomicExch(err, 1);
@@ -506,7 +512,8 @@ __global__ void mlp_pack_kernel(const float* __restrict__ p, __nv_bfloat16* __re
 // ------------------------------------------------------------------ host
 struct MlpHandle;
 namespace snakesim {
-SimStatus mlp_forward_launch(MlpHandle* h, const void* feat, long long rows, float* out, cudaStream_t st);
+SimStatus mlp_forward_launch(MlpHandle* h, const void* feat, long long rows, float* out, cudaStream_t st,
+                             int bilateral);
 }
 struct MlpHandle {
   cudaStream_t stream = nullptr;
@@ -545,12 +552,12 @@ SimStatus check_err(MlpHandle* h) {
 }  // namespace
 
 SimStatus snakesim::mlp_forward_launch(MlpHandle* h, const void* feat, long long rows, float* out,
-                                       cudaStream_t st) {
+                                       cudaStream_t st, int bilateral) {
   if (rows <= 0) return SIM_OK;
   const long long tiles = (rows + kTile - 1) / kTile;
   const int grid = (int)std::min<long long>(tiles, 2LL * h->sms);
   mlp_infer_kernel<<<grid, kInferThreads, sizeof(InferSmem), st>>>((const __nv_bfloat16*)feat, rows, dev_of(h),
-                                                                  out, h->err);
+                                                                  out, h->err, bilateral);
   MCU(cudaGetLastError());
   return SIM_OK;
 }
@@ -615,7 +622,7 @@ SimStatus mlp_get_params(MlpHandle* h, float* params, int is_device) {
 SimStatus mlp_forward(MlpHandle* h, const void* feat, int64_t rows, float* out) {
   if (!h || !feat || !out || rows < 0) return mfail(SIM_EINVAL, "bad arguments");
   if (((uintptr_t)feat & 15u) != 0) return mfail(SIM_EINVAL, "feat is not 16-byte aligned");
-  SimStatus s = snakesim::mlp_forward_launch(h, feat, rows, out, h->stream);
+  SimStatus s = snakesim::mlp_forward_launch(h, feat, rows, out, h->stream, 0);
   if (s != SIM_OK) return s;
   return check_err(h);
 }
@@ -782,7 +789,7 @@ extern "C" SimStatus mlp_forward_noalloc(const float* params, int32_t n_params, 
   d.b1 = params + kOffB1; d.b2 = params + kOffB2; d.w3 = params + kOffW3; d.b3 = params + kOffB3;
   const long long tiles = (rows + kTile - 1) / kTile;
   const int grid = (int)std::min<long long>(tiles, 2LL * sms);
-  mlp_infer_kernel<<<grid, kInferThreads, sizeof(InferSmem), st>>>((const __nv_bfloat16*)feat, rows, d, out, err);
+  mlp_infer_kernel<<<grid, kInferThreads, sizeof(InferSmem), st>>>((const __nv_bfloat16*)feat, rows, d, out, err, 0);
   MCU(cudaGetLastError());
   int e = 0;
   MCU(cudaMemcpyAsync(&e, err, sizeof(int), cudaMemcpyDeviceToHost, st));

@@ -323,6 +323,9 @@ SimStatus validate_cfg(const SimConfig* c) {
     return fail(SIM_EINVAL, "invalid config: solver must be SIM_SOLVER_JACOBI or SIM_SOLVER_NEWTON_PCR");
   if (c->solver == SIM_SOLVER_NEWTON_PCR && (c->contact != 0 || c->pcr_iters < 1))
     return fail(SIM_EINVAL, "the Newton + PCR solver needs contact = 0 and pcr_iters >= 1");
+  if ((c->net_rows != SIM_NET_ROWS_ALL && c->net_rows != SIM_NET_ROWS_BILATERAL) || c->net_every < 0)
+    return fail(SIM_EINVAL, "invalid config: net_rows must be SIM_NET_ROWS_ALL or SIM_NET_ROWS_BILATERAL, "
+                            "net_every >= 0");
   if (c->latency != SIM_LATENCY_EXP && c->latency != SIM_LATENCY_LAW)
     return fail(SIM_EINVAL, "invalid config: latency must be SIM_LATENCY_EXP or SIM_LATENCY_LAW");
   if (c->latency == SIM_LATENCY_LAW &&
@@ -485,6 +488,9 @@ SolverArgs make_args(SimHandle* h, int n_steps) {
   A.law_every = std::max(1, (int)std::llround((double)h->cfg.law_dt / A.h_d));
   A.k_i = h->cfg.k_inflate; A.k_d = h->cfg.k_deflate; A.t_p = h->cfg.t_p; A.p_s = h->cfg.p_source;
   A.pcr_iters = h->cfg.pcr_iters;
+  A.net_rows = h->cfg.net_rows;
+  A.net_every = std::max(1, h->cfg.net_every);
+  A.span = 1;
   return A;
 }
 
@@ -535,19 +541,23 @@ SimStatus advance(SimHandle* h, int n, cudaStream_t st) {
   return SIM_OK;
 }
 
-// One env-step substep by substep, with the network between solver launches.  Each
-// layout's chain (solver kernel, network, solver kernel, ...) runs on its own stream
-// for the whole env-step: a substep of one layout waits only for its own snakes, and the
-// other layouts' work fills the tail of its launches.
+// One env-step in spans of net_every substeps, with the network between solver launches:
+// a launch finishes the substep the network has just started and the substeps up to the
+// next network substep (those from beta lambda_prev), then begins that one and writes its
+// features.  Each layout's chain (solver kernel, network, solver kernel, ...) runs on its
+// own stream for the whole env-step: a span of one layout waits only for its own snakes,
+// and the other layouts' work fills the tail of its launches.
 SimStatus split_step(SimHandle* h, cudaStream_t st) {
   if (h->n_items == 0) return SIM_OK;
   SimStatus r = schedule(h, st);
   if (r == SIM_OK) r = fork_layouts(h, st);
   const bool learned = h->cfg.warm == SIM_WARM_LEARNED;
-  for (int sub = -1; sub < h->cfg.n_sub && r == SIM_OK; ++sub) {
+  const int every = std::max(1, h->cfg.net_every);
+  for (int sub = -1; sub < h->cfg.n_sub && r == SIM_OK; sub = sub < 0 ? 0 : sub + every) {
     SolverArgs A = make_args(h, 0);
     A.split = 1;
     A.sub = sub;
+    A.span = every;
     for (int k = 0; k < h->n_lay && r == SIM_OK; ++k) {
       const int l = h->lay_launch[k];
       cudaStream_t s = lay_stream(h, l, st);
@@ -639,7 +649,9 @@ SimStatus launch_args(SimHandle* h, const SolverArgs& A, cudaStream_t st) {
 SimStatus launch_net(SimHandle* h, int l, cudaStream_t s) {
   const long long r0 = 6LL * h->lay_fnode[l], r1 = 6LL * h->lay_fnode[l + 1];
   if (r1 <= r0) return SIM_OK;
-  SimStatus r = mlp_forward_launch(h->mlp, h->feat + r0 * 32, r1 - r0, h->lam0 + r0, s);
+  const int bilateral = h->cfg.net_rows == SIM_NET_ROWS_BILATERAL;
+  SimStatus r = mlp_forward_launch(h->mlp, h->feat + r0 * 32, bilateral ? (r1 - r0) / 2 : r1 - r0,
+                                   h->lam0 + r0, s, bilateral);
   h->launches += 1;
   return r;
 }
@@ -1051,7 +1063,8 @@ SimStatus sim_split_finish(SimHandle* h) {
   if (h->cur_sub < 0) return fail(SIM_EINVAL, "no env-step in progress (sim_split_begin)");
   const bool learned = h->cfg.warm == SIM_WARM_LEARNED;
   if (learned && !h->mlp) return fail(SIM_EINVAL, "learned warm start without a network (sim_set_mlp)");
-  SimStatus st = launch_split(h, h->cur_sub, h->stream, learned);
+  const bool net = learned && h->cur_sub % std::max(1, h->cfg.net_every) == 0;
+  SimStatus st = launch_split(h, h->cur_sub, h->stream, net);
   if (st != SIM_OK) return st;
   h->cur_sub += 1;
   if (h->cur_sub >= h->cfg.n_sub) {

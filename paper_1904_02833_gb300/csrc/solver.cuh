@@ -116,6 +116,7 @@ struct SnakeK {
   int N, seg, nfix, L, nb, lb, fb;  // fb: first node of the snake in the feature row order
   float L0, inv_L0, inv_m, mass, at_s, at_b, mu, radius, gain, e_inf, e_def, damp_over_h;
   float mu_side, inv_mu, inv_mu_side;  // mu_side > 0: anisotropic friction (body frame)
+  float om_m;                          // omega m: relaxed contact / friction update per unit slip
 };
 
 // Friction pair (px, py) limited to the Coulomb set of normal multiplier ln: the disc
@@ -214,7 +215,7 @@ __device__ __forceinline__ float row_pass(const SnakeK& S, const SolverArgs& A, 
       if (WARM) d = lam[j][0];
       else {
         const float l = lam[j][0];
-        r = fmaxf(r, on ? fabsf(c + S.at_s * l) * S.inv_L0 : 0.f);
+        r = fmaxf(r, on ? fabsf(c + S.at_s * l) : 0.f);
         d = __fdividef(A.omega * (-c - S.at_s * l), wg + S.at_s);
       }
       d = on ? d : 0.f;
@@ -239,7 +240,7 @@ __device__ __forceinline__ float row_pass(const SnakeK& S, const SolverArgs& A, 
       if (WARM) d = lam[j][1];
       else {
         const float l = lam[j][1];
-        r = fmaxf(r, on ? fabsf(c + S.at_b * l) * S.inv_L0 : 0.f);
+        r = fmaxf(r, on ? fabsf(c + S.at_b * l) : 0.f);
         d = __fdividef(A.omega * (-c - S.at_b * l), wg + S.at_b);
       }
       d = on ? d : 0.f;
@@ -262,7 +263,7 @@ __device__ __forceinline__ float row_pass(const SnakeK& S, const SolverArgs& A, 
       if (WARM) d = lam[j][2];
       else {
         const float l = lam[j][2];
-        r = fmaxf(r, on ? fabsf(c + S.at_b * l) * S.inv_L0 : 0.f);
+        r = fmaxf(r, on ? fabsf(c + S.at_b * l) : 0.f);
         d = __fdividef(A.omega * (-c - S.at_b * l), wg + S.at_b);
       }
       d = on ? d : 0.f;
@@ -294,19 +295,19 @@ __device__ __forceinline__ float row_pass(const SnakeK& S, const SolverArgs& A, 
         }
         // residuals: Fischer-Burmeister on (c_n, w lambda_n); natural map of the cone
         const float b = wi * ln;
-        r = fmaxf(r, on ? fabsf(cn + b - sqrtf(cn * cn + b * b)) * S.inv_L0 : 0.f);
+        r = fmaxf(r, on ? fabsf(cn + b - sqrtf(cn * cn + b * b)) : 0.f);
         const float ax = wi * lam[j][4], ay = wi * lam[j][5];
         float px = ax - ux, py = ay - uy;
         friction_limit<ANISO>(S, bx, by, wi * ln, px, py);
         // squared friction residual; one square root per pass for the whole lane
         q2 = fmaxf(q2, on ? (ax - px) * (ax - px) + (ay - py) * (ay - py) : 0.f);
         // contact: lambda_n <- max(0, lambda_n + omega (-c_n / w))
-        const float nl = fmaxf(0.f, ln - A.omega * cn * S.mass);
+        const float nl = fmaxf(0.f, ln - S.om_m * cn);
         dn = nl - ln;
         // friction: relaxed update limited to the Coulomb set of the current iterate's
         // lambda_n
-        float tx = lam[j][4] - A.omega * ux * S.mass;
-        float ty = lam[j][5] - A.omega * uy * S.mass;
+        float tx = lam[j][4] - S.om_m * ux;
+        float ty = lam[j][5] - S.om_m * uy;
         friction_limit<ANISO>(S, bx, by, ln, tx, ty);
         fx = tx - lam[j][4]; fy = ty - lam[j][5];
       }
@@ -319,7 +320,8 @@ __device__ __forceinline__ float row_pass(const SnakeK& S, const SolverArgs& A, 
     sp = sc;
   }
   if (!WARM) {
-    r = fmaxf(r, sqrtf(q2) * S.inv_L0);
+    // every term is a length: one scaling by 1 / L0 (monotone, so the max is the same)
+    r = fmaxf(r, sqrtf(q2)) * S.inv_L0;
     if (!(r <= 3.0e38f)) r = INFINITY;  // NaN -> inf so that the max keeps it
     // one ballot decides every group's stop; the group's max residual is reduced only in
     // the (rare) passes where some live group stops, to be recorded
@@ -625,10 +627,10 @@ __device__ void newton_pcr(const SnakeK& S, const SolverArgs& A, int q, bool val
 
 // Advances the snake owned by this lane group.  Fused mode (A.split == 0): A.n_steps
 // env-steps with all substeps in registers.  Split mode: finishes substep A.sub (if >= 0)
-// of the current env-step and, if A.sub + 1 < n_sub, begins substep A.sub + 1 (gait,
-// filter, prediction), writes its features and leaves the state in HBM at that point
-// (positions = substep start, velocities = predicted), so that the warm-start network
-// can run between two launches.
+// of the current env-step and the substeps after it up to A.sub + A.span - 1, then, if
+// the next one exists, begins it (gait, filter, prediction), writes its features and
+// leaves the state in HBM at that point (positions = substep start, velocities =
+// predicted), so that the warm-start network can run between two launches.
 // VAR: which solve the kernel carries.  kVarJacobi: the Jacobi relaxation with isotropic
 // friction; kVarAniso: the same with the anisotropic friction path (batches where some
 // snake has mu_side > 0; the other kernels carry none of its code); kVarPcr: Newton +
@@ -658,6 +660,7 @@ __device__ void run_group(const SolverArgs& A, int snake, bool valid, float* sme
   S.inv_mu = S.mu_side > 0.f ? 1.0f / P.mu : 0.f;
   S.inv_mu_side = S.mu_side > 0.f ? 1.0f / S.mu_side : 0.f;
   S.e_inf = expf(-h / P.tau_inf); S.e_def = expf(-h / P.tau_def);
+  S.om_m = A.omega * S.mass;
   S.damp_over_h = expf(-P.damping * h) / h;
 
   // x = xs + dx; between substeps dx holds the last substep's displacement
@@ -744,8 +747,9 @@ __device__ void run_group(const SolverArgs& A, int snake, bool valid, float* sme
     }
   };
 
-  // warm start, (a5, a6) Jacobi iterations, (a7) velocity with damping
-  auto finish_substep = [&](float& rmax, int& itot) {
+  // warm start, (a5, a6) Jacobi iterations, (a7) velocity with damping; `net`: the learned
+  // warm start adds the network's prediction at this substep
+  auto finish_substep = [&](float& rmax, int& itot, bool net) {
     float xsl[3], xsr[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
@@ -767,7 +771,8 @@ __device__ void run_group(const SolverArgs& A, int snake, bool valid, float* sme
 #pragma unroll
         for (int k = 0; k < 6; ++k) {
           float l = A.beta * lam[j][k];
-          if (A.warm == 2 && A.lam0 && valid && i < S.N) l += A.lam0[(size_t)(S.fb + i) * 6 + k] * sc;
+          if (A.warm == 2 && net && A.lam0 && valid && i < S.N && (A.net_rows == SIM_NET_ROWS_ALL || k < 3))
+            l += A.lam0[(size_t)(S.fb + i) * 6 + k] * sc;
           lam[j][k] = l;
         }
       }
@@ -817,14 +822,22 @@ __device__ void run_group(const SolverArgs& A, int snake, bool valid, float* sme
       itot = 0;
       for (int s = 0; s < A.n_sub; ++s) {
         begin_substep(step0 + st, s);
-        finish_substep(rmax, itot);
+        finish_substep(rmax, itot, false);
       }
     }
   } else {
     if (A.sub > 0 && valid && q == 0) { rmax = A.resid[snake]; itot = A.iters[snake]; }
-    if (A.sub >= 0) finish_substep(rmax, itot);
-    if (A.sub + 1 < A.n_sub) {
-      begin_substep(step0, A.sub + 1);
+    int next = A.sub + 1;
+    if (A.sub >= 0) {
+      // the substep begun by the previous launch, then the rest of the span in full
+      finish_substep(rmax, itot, A.sub % A.net_every == 0);
+      for (; next < A.sub + A.span && next < A.n_sub; ++next) {
+        begin_substep(step0, next);
+        finish_substep(rmax, itot, next % A.net_every == 0);
+      }
+    }
+    if (next < A.n_sub) {
+      begin_substep(step0, next);
       if (SPLIT) write_features<NPL, G>(S, A, q, valid, xs, dx, v, lam, th);
       at_boundary = false;
     }

@@ -92,19 +92,20 @@ def pad_features(f24: torch.Tensor) -> torch.Tensor:
 
 
 def collect(sim, n_steps: int, substeps=None, every: int = 1, target_tol: float = 1e-6,
-            target_iters: int = 20000, skip: float | None = None):
+            target_iters: int = 20000, skip: float | None = None, target_warm: int = 0):
     """Logs training pairs along the simulator's own trajectory (its current settings:
     tolerance, warm start and, in the learned mode, its network), so the features carry
     the previous multipliers the deployed solver produces.  At each logged substep the
-    substep is also solved from the same start to `target_tol` (cold start) on a
-    snapshot; sim_training_rows then writes every existing row's features and its target
+    substep is also solved from the same start to `target_tol` on a snapshot (from zero
+    multipliers, target_warm = 0, or from beta times the previous ones, target_warm = 1);
+    sim_training_rows then writes every existing row's features and its target
     (the multiplier reached there minus beta times the previous multiplier, over
     m g h^2: the network predicts the correction to the beta-weighted previous
     multiplier).  Returns bf16 features [n, 32] and float targets [n], on the device."""
     w = dict(sim.settings)
     n_sub = w["n_sub"]
     beta = float(w.get("beta", 1.0)) if skip is None else float(skip)
-    target_cfg = dict(w, tol=float(target_tol), iters=int(target_iters), warm=0)
+    target_cfg = dict(w, tol=float(target_tol), iters=int(target_iters), warm=int(target_warm), beta=beta)
     feats, targets = [], []
     substeps = list(range(n_sub)) if substeps is None else list(substeps)
     for k in range(n_steps):
@@ -151,15 +152,17 @@ def train(mlp: WarmStartMLP, feat, target, epochs: int = 10, batch: int = 16384,
 
 def train_warm_start(n_snakes: int = 1024, seeds=None, rounds: int = 2, settle: int = 6,
                      steps: int = 10, tol: float = 1e-4, epochs0: int = 20, epochs: int = 10,
-                     batch: int = 16384, log=None, make_batch=None, skip: float = 0.5):
+                     batch: int = 16384, log=None, make_batch=None, skip: float = 0.5,
+                     target_warm: int = 0):
     """Trains the warm-start network on data the plain solver generates.
 
     Round 0 follows cold-start trajectories; every later round follows trajectories of
     the learned warm start itself (on new seeds), so the network sees the previous
     multipliers it will meet when deployed.  Targets: at a logged substep, the
-    multipliers the plain cold-start solver reaches at `tol` from the same start,
-    minus `skip` times the previous multipliers (the learned warm start adds the network's
-    output to the previous multipliers weighted by beta = skip).  All simulation and all
+    multipliers the plain solver reaches at `tol` from the same start (cold, or from
+    `skip` times the previous multipliers with target_warm = 1), minus `skip` times the
+    previous multipliers (the learned warm start adds the network's output to the
+    previous multipliers weighted by beta = skip).  All simulation and all
     training run in the library's kernels.  Returns the network and a record of the
     rounds."""
     import workloads as W  # seeded parameter generator (no simulation arithmetic)
@@ -177,7 +180,8 @@ def train_warm_start(n_snakes: int = 1024, seeds=None, rounds: int = 2, settle: 
             sim.set_mlp(net)
             sim.set_config(warm=2, beta=skip)
             sim.step(2)
-        f, t = collect(sim, steps, substeps=(0, 7, 14), every=2, target_tol=tol, skip=skip)
+        f, t = collect(sim, steps, substeps=(0, 7, 14), every=2, target_tol=tol, skip=skip,
+                       target_warm=target_warm)
         sim.close()
         return f, t
 

@@ -59,6 +59,8 @@ def make_config(s: dict) -> N.SimConfig:
     c.law_dt = float(s.get("law_dt", 0.0083))
     c.solver = int(s.get("solver", 0))
     c.pcr_iters = int(s.get("pcr_iters", 20))
+    c.net_rows = int(s.get("net_rows", 0))
+    c.net_every = int(s.get("net_every", 1))
     return c
 
 
