@@ -9,7 +9,7 @@
 // arrives as d L / d tip(t) for the last node after every env-step.
 //
 // One warp owns one snake (one CTA per snake); node and row arrays live in shared memory
-// and the lanes stride over nodes, with __syncwarp() between phases.  The backward pass
+// and the lanes stride over nodes, with __syncthreads() between phases.  The backward pass
 // of a checkpoint segment recomputes the segment's substep-start states, then walks the
 // substeps in reverse; inside a substep it recomputes the K iterates (stored in an
 // L2-resident scratch) and runs the transposed iteration:
@@ -76,7 +76,10 @@ struct Sh {  // shared-memory arrays of one snake
   float *xb, *vb, *pb, *lb, *gb, *cb, *dbar, *lbn, *xn, *xsb, *thb;
 };
 
-__device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
+// Threads per snake (one block per snake): the lanes stride over the snake's nodes and
+// rows, and the phases of a substep are separated by block barriers.
+constexpr int kAdjThreads = 64;
+__device__ __forceinline__ int tid() { return threadIdx.x; }
 
 __device__ Snk load_snake(const AdjArgs& A, int s) {
   const SnakeParams P = A.prm[s];
@@ -141,7 +144,7 @@ __device__ __forceinline__ void beta_hess_vec(const float* e, const float* u, fl
 // the pressures before the filter.
 __device__ void begin_pressure(const Snk& S, const AdjArgs& A, long long step, int s, const Sh& M) {
   const double t = ((double)step * A.n_sub + (double)(s + 1)) * A.h_d;
-  for (int k = lane_id(); k < S.L; k += 32) {
+  for (int k = tid(); k < S.L; k += kAdjThreads) {
     const float a = gait(S, k, t);
     const float tg[2] = {fmaxf(a, 0.f), fmaxf(-a, 0.f)};
     for (int c = 0; c < 2; ++c) {
@@ -151,8 +154,8 @@ __device__ void begin_pressure(const Snk& S, const AdjArgs& A, long long step, i
       M.p[2 * k + c] = tg[c] + (pp - tg[c]) * expf(-A.h / tau);
     }
   }
-  __syncwarp();
-  for (int i = lane_id(); i < S.N; i += 32) {
+  __syncthreads();
+  for (int i = tid(); i < S.N; i += kAdjThreads) {
     float th = 0.f;
     if (i >= 1 && i <= S.N - 2 && i % S.seg != 0) {
       const int k = i / S.seg;
@@ -160,13 +163,13 @@ __device__ void begin_pressure(const Snk& S, const AdjArgs& A, long long step, i
     }
     M.th[i] = th;
   }
-  __syncwarp();
+  __syncthreads();
 }
 
 // rows of every node at (X, lam): values, gradients, diagonal, relaxed update, branches
 __device__ void eval_rows(const Snk& S, const AdjArgs& A, const Sh& M) {
   const float h2 = A.h * A.h;
-  for (int i = lane_id(); i < S.N; i += 32) {
+  for (int i = tid(); i < S.N; i += kAdjThreads) {
     for (int k = 0; k < 6; ++k) {
       const int j = i * 6 + k;
       M.c[j] = 0.f; M.D[j] = 0.f; M.dl[j] = 0.f; M.lnew[j] = M.lam[j]; M.br[j] = 0;
@@ -236,12 +239,12 @@ __device__ void eval_rows(const Snk& S, const AdjArgs& A, const Sh& M) {
       M.lnew[jx] = nx; M.lnew[jy] = ny; M.dl[jx] = nx - M.lam[jx]; M.dl[jy] = ny - M.lam[jy];
     }
   }
-  __syncwarp();
+  __syncthreads();
 }
 
 // x_i += w_i sum_j g_ji dl_j (fixed order), lambda <- lambda_new
 __device__ void apply_rows(const Snk& S, const AdjArgs& A, const Sh& M) {
-  for (int i = lane_id(); i < S.N; i += 32) {
+  for (int i = tid(); i < S.N; i += kAdjThreads) {
     const int list[11][3] = {{i - 1, 0, 1}, {i, 0, 0}, {i - 1, 1, 2}, {i - 1, 2, 2}, {i, 1, 1}, {i, 2, 1},
                              {i + 1, 1, 0}, {i + 1, 2, 0}, {i, 3, 0}, {i, 4, 0}, {i, 5, 0}};
     float acc[3] = {0.f, 0.f, 0.f};
@@ -256,38 +259,38 @@ __device__ void apply_rows(const Snk& S, const AdjArgs& A, const Sh& M) {
     for (int d = 0; d < 3; ++d) M.X[3 * i + d] += wi * acc[d];
     for (int k = 0; k < 6; ++k) M.lam[i * 6 + k] = M.lnew[i * 6 + k];
   }
-  __syncwarp();
+  __syncthreads();
 }
 
 // One substep forward from (M.X = x, M.v, M.p).  With `it`, stores the K + 1 iterates.
 __device__ void substep_fwd(const Snk& S, const AdjArgs& A, long long step, int s, const Sh& M, float* it) {
   begin_pressure(S, A, step, s, M);
   const float h = A.h;
-  for (int i = lane_id(); i < S.N; i += 32)
+  for (int i = tid(); i < S.N; i += kAdjThreads)
     for (int d = 0; d < 3; ++d) {
       M.xs[3 * i + d] = M.X[3 * i + d];
       if (i >= S.nfix) { M.v[3 * i + d] += h * A.g[d]; M.X[3 * i + d] += h * M.v[3 * i + d]; }
     }
-  for (int i = lane_id(); i < S.N * 6; i += 32) M.lam[i] = 0.f;
-  __syncwarp();
+  for (int i = tid(); i < S.N * 6; i += kAdjThreads) M.lam[i] = 0.f;
+  __syncthreads();
   for (int k = 0; k < A.K; ++k) {
     if (it) {
       float* dst = it + (size_t)k * A.n_max * 9;
-      for (int i = lane_id(); i < S.N * 3; i += 32) dst[i] = M.X[i];
-      for (int i = lane_id(); i < S.N * 6; i += 32) dst[A.n_max * 3 + i] = M.lam[i];
+      for (int i = tid(); i < S.N * 3; i += kAdjThreads) dst[i] = M.X[i];
+      for (int i = tid(); i < S.N * 6; i += kAdjThreads) dst[A.n_max * 3 + i] = M.lam[i];
     }
     eval_rows(S, A, M);
     apply_rows(S, A, M);
   }
   if (it) {
     float* dst = it + (size_t)A.K * A.n_max * 9;
-    for (int i = lane_id(); i < S.N * 3; i += 32) dst[i] = M.X[i];
+    for (int i = tid(); i < S.N * 3; i += kAdjThreads) dst[i] = M.X[i];
   }
   const float cd = expf(-S.d * h) / h;
-  for (int i = lane_id(); i < S.N; i += 32)
+  for (int i = tid(); i < S.N; i += kAdjThreads)
     for (int d = 0; d < 3; ++d)
       M.v[3 * i + d] = i >= S.nfix ? (M.X[3 * i + d] - M.xs[3 * i + d]) * cd : 0.f;
-  __syncwarp();
+  __syncthreads();
 }
 
 // Adjoint of one substep.  On entry M.xb, M.vb, M.pb hold the adjoints of the substep's
@@ -301,7 +304,7 @@ __device__ void substep_adj(const Snk& S, const AdjArgs& A, long long step, int 
   substep_fwd(S, A, step, s, M, it);  // M.pin: filter inputs; M.p: filtered; M.xs: start x
   const float* XK = it + (size_t)A.K * A.n_max * 9;
   const float cd = expf(-S.d * h) / h;
-  for (int i = lane_id(); i < S.N; i += 32)
+  for (int i = tid(); i < S.N; i += kAdjThreads)
     for (int d = 0; d < 3; ++d) {
       M.xsb[3 * i + d] = 0.f;
       if (i >= S.nfix) {
@@ -311,17 +314,17 @@ __device__ void substep_adj(const Snk& S, const AdjArgs& A, long long step, int 
         tb[1] += gv * (XK[3 * i + d] - M.xs[3 * i + d]) * (-h) * cd;
       }
     }
-  for (int i = lane_id(); i < S.N * 6; i += 32) M.lb[i] = 0.f;
-  for (int i = lane_id(); i < S.N; i += 32) M.thb[i] = 0.f;
-  __syncwarp();
+  for (int i = tid(); i < S.N * 6; i += kAdjThreads) M.lb[i] = 0.f;
+  for (int i = tid(); i < S.N; i += kAdjThreads) M.thb[i] = 0.f;
+  __syncthreads();
   for (int k = A.K - 1; k >= 0; --k) {
     const float* src = it + (size_t)k * A.n_max * 9;
-    for (int i = lane_id(); i < S.N * 3; i += 32) M.X[i] = src[i];
-    for (int i = lane_id(); i < S.N * 6; i += 32) M.lam[i] = src[A.n_max * 3 + i];
-    __syncwarp();
+    for (int i = tid(); i < S.N * 3; i += kAdjThreads) M.X[i] = src[i];
+    for (int i = tid(); i < S.N * 6; i += kAdjThreads) M.lam[i] = src[A.n_max * 3 + i];
+    __syncthreads();
     eval_rows(S, A, M);
     // delta^ and g^ from x^(k+1), lambda^(k+1)
-    for (int o = lane_id(); o < S.N; o += 32)
+    for (int o = tid(); o < S.N; o += kAdjThreads)
       for (int kk = 0; kk < 6; ++kk) {
         const int j = o * 6 + kk;
         for (int q = 0; q < 9; ++q) M.gb[j * 9 + q] = 0.f;
@@ -340,9 +343,9 @@ __device__ void substep_adj(const Snk& S, const AdjArgs& A, long long step, int 
         }
         M.dbar[j] = db;
       }
-    __syncwarp();
+    __syncthreads();
     // through the row updates
-    for (int o = lane_id(); o < S.N; o += 32) {
+    for (int o = tid(); o < S.N; o += kAdjThreads) {
       for (int kk = 0; kk < 6; ++kk) M.lbn[o * 6 + kk] = M.lb[o * 6 + kk];
       for (int kk = 0; kk < 3; ++kk) {
         const int j = o * 6 + kk;
@@ -386,9 +389,9 @@ __device__ void substep_adj(const Snk& S, const AdjArgs& A, long long step, int 
         M.cb[jx] += -om * tbx * S.m; M.cb[jy] += -om * tby * S.m;
       }
     }
-    __syncwarp();
+    __syncthreads();
     // x^k adjoint: x^(k+1) adjoint + sum_j g_j c^_j + H_j g^_j, gathered per node
-    for (int i = lane_id(); i < S.N; i += 32) {
+    for (int i = tid(); i < S.N; i += kAdjThreads) {
       float acc[3] = {M.xb[3 * i], M.xb[3 * i + 1], M.xb[3 * i + 2]};
       const int list[11][3] = {{i - 1, 0, 1}, {i, 0, 0}, {i - 1, 1, 2}, {i - 1, 2, 2}, {i, 1, 1}, {i, 2, 1},
                                {i + 1, 1, 0}, {i + 1, 2, 0}, {i, 3, 0}, {i, 4, 0}, {i, 5, 0}};
@@ -438,21 +441,21 @@ __device__ void substep_adj(const Snk& S, const AdjArgs& A, long long step, int 
         M.xsb[3 * i + 1] -= M.cb[i * 6 + 5];
       }
     }
-    __syncwarp();
-    for (int i = lane_id(); i < S.N * 3; i += 32) M.xb[i] = M.xn[i];
-    for (int i = lane_id(); i < S.N * 6; i += 32) M.lb[i] = M.lbn[i];
-    __syncwarp();
+    __syncthreads();
+    for (int i = tid(); i < S.N * 3; i += kAdjThreads) M.xb[i] = M.xn[i];
+    for (int i = tid(); i < S.N * 6; i += kAdjThreads) M.lb[i] = M.lbn[i];
+    __syncthreads();
   }
   // prediction: x0 = x_in + h v1 (free), v1 = v_in + h g
-  for (int i = lane_id(); i < S.N; i += 32)
+  for (int i = tid(); i < S.N; i += kAdjThreads)
     for (int d = 0; d < 3; ++d) {
       const float x0b = M.xb[3 * i + d];
       M.xb[3 * i + d] = x0b + M.xsb[3 * i + d];
       M.vb[3 * i + d] = i >= S.nfix ? h * x0b : 0.f;
     }
-  __syncwarp();
+  __syncthreads();
   // rest angles theta = G (p_R' - p_L') L0 and the latency filter
-  if (lane_id() == 0) {
+  if (tid() == 0) {
     for (int i = 1; i <= S.N - 2; ++i) {
       if (i % S.seg == 0) continue;
       const int k = i / S.seg;
@@ -462,9 +465,9 @@ __device__ void substep_adj(const Snk& S, const AdjArgs& A, long long step, int 
       M.pb[2 * k + 1] -= t * S.G * S.L0;
     }
   }
-  __syncwarp();
+  __syncthreads();
   const double tt = ((double)step * A.n_sub + (double)(s + 1)) * A.h_d;
-  for (int k = lane_id(); k < S.L; k += 32) {
+  for (int k = tid(); k < S.L; k += kAdjThreads) {
     const float a = gait(S, k, tt);
     const float tg[2] = {fmaxf(a, 0.f), fmaxf(-a, 0.f)};
     for (int c = 0; c < 2; ++c) {
@@ -476,7 +479,7 @@ __device__ void substep_adj(const Snk& S, const AdjArgs& A, long long step, int 
       tb[inf ? 2 : 3] += g * (pp - tg[c]) * e * h / (tau * tau);
     }
   }
-  __syncwarp();
+  __syncthreads();
 }
 
 __device__ Sh carve(uint8_t* base, int n, int l) {
@@ -502,7 +505,7 @@ size_t adjoint_smem_bytes(int n_max, int l_max) {
 
 // Forward over a segment: state in A.x/A.v/A.p (per snake), tips written, substep starts
 // recorded when A.store.
-__global__ void __launch_bounds__(32) adj_forward_kernel(AdjArgs A) {
+__global__ void __launch_bounds__(kAdjThreads) adj_forward_kernel(AdjArgs A) {
   const int s = blockIdx.x;
   if (s >= A.n_snakes) return;
   extern __shared__ __align__(16) uint8_t smem[];
@@ -511,34 +514,34 @@ __global__ void __launch_bounds__(32) adj_forward_kernel(AdjArgs A) {
   float* gx = A.x + (size_t)s * A.n_max * 3;
   float* gv = A.v + (size_t)s * A.n_max * 3;
   float* gp = A.p + (size_t)s * A.l_max * 2;
-  for (int i = lane_id(); i < S.N * 3; i += 32) { M.X[i] = gx[i]; M.v[i] = gv[i]; }
-  for (int i = lane_id(); i < S.L * 2; i += 32) M.p[i] = gp[i];
-  __syncwarp();
+  for (int i = tid(); i < S.N * 3; i += kAdjThreads) { M.X[i] = gx[i]; M.v[i] = gv[i]; }
+  for (int i = tid(); i < S.L * 2; i += kAdjThreads) M.p[i] = gp[i];
+  __syncthreads();
   for (int st = 0; st < A.n_steps; ++st) {
     for (int sb = 0; sb < A.n_sub; ++sb) {
       if (A.store) {
         const size_t q = (size_t)s * A.n_rec + (size_t)st * A.n_sub + sb;
-        for (int i = lane_id(); i < S.N * 3; i += 32) {
+        for (int i = tid(); i < S.N * 3; i += kAdjThreads) {
           A.rec_x[q * A.n_max * 3 + i] = M.X[i];
           A.rec_v[q * A.n_max * 3 + i] = M.v[i];
         }
-        for (int i = lane_id(); i < S.L * 2; i += 32) A.rec_p[q * A.l_max * 2 + i] = M.p[i];
+        for (int i = tid(); i < S.L * 2; i += kAdjThreads) A.rec_p[q * A.l_max * 2 + i] = M.p[i];
       }
       substep_fwd(S, A, A.step0 + st, sb, M, nullptr);
     }
-    if (A.tips && lane_id() == 0) {
+    if (A.tips && tid() == 0) {
       float* t = A.tips + ((size_t)(A.tip_base + st) * A.n_snakes + s) * 3;
       t[0] = M.X[3 * (S.N - 1)]; t[1] = M.X[3 * (S.N - 1) + 1]; t[2] = M.X[3 * (S.N - 1) + 2];
     }
-    __syncwarp();
+    __syncthreads();
   }
-  for (int i = lane_id(); i < S.N * 3; i += 32) { gx[i] = M.X[i]; gv[i] = M.v[i]; }
-  for (int i = lane_id(); i < S.L * 2; i += 32) gp[i] = M.p[i];
+  for (int i = tid(); i < S.N * 3; i += kAdjThreads) { gx[i] = M.X[i]; gv[i] = M.v[i]; }
+  for (int i = tid(); i < S.L * 2; i += kAdjThreads) gp[i] = M.p[i];
 }
 
 // Backward over a segment whose substep starts were recorded; adjoints carried in
 // A.xb/A.vb/A.pb, parameter adjoints added to A.grad.
-__global__ void __launch_bounds__(32) adj_backward_kernel(AdjArgs A) {
+__global__ void __launch_bounds__(kAdjThreads) adj_backward_kernel(AdjArgs A) {
   const int s = blockIdx.x;
   if (s >= A.n_snakes) return;
   extern __shared__ __align__(16) uint8_t smem[];
@@ -548,34 +551,43 @@ __global__ void __launch_bounds__(32) adj_backward_kernel(AdjArgs A) {
   float* gvb = A.vb + (size_t)s * A.n_max * 3;
   float* gpb = A.pb + (size_t)s * A.l_max * 2;
   float* it = A.iters + (size_t)s * (A.K + 1) * A.n_max * 9;
-  for (int i = lane_id(); i < S.N * 3; i += 32) { M.xb[i] = gxb[i]; M.vb[i] = gvb[i]; }
-  for (int i = lane_id(); i < S.L * 2; i += 32) M.pb[i] = gpb[i];
-  __syncwarp();
+  for (int i = tid(); i < S.N * 3; i += kAdjThreads) { M.xb[i] = gxb[i]; M.vb[i] = gvb[i]; }
+  for (int i = tid(); i < S.L * 2; i += kAdjThreads) M.pb[i] = gpb[i];
+  __syncthreads();
   float tb[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
   for (int st = A.n_steps - 1; st >= 0; --st) {
-    if (lane_id() == 0) {
+    if (tid() == 0) {
       const float* t = A.tips_bar + ((size_t)(A.tip_base + st) * A.n_snakes + s) * 3;
       for (int d = 0; d < 3; ++d) M.xb[3 * (S.N - 1) + d] += t[d];
     }
-    __syncwarp();
+    __syncthreads();
     for (int sb = A.n_sub - 1; sb >= 0; --sb) {
       const size_t q = (size_t)s * A.n_rec + (size_t)st * A.n_sub + sb;
-      for (int i = lane_id(); i < S.N * 3; i += 32) {
+      for (int i = tid(); i < S.N * 3; i += kAdjThreads) {
         M.X[i] = A.rec_x[q * A.n_max * 3 + i];
         M.v[i] = A.rec_v[q * A.n_max * 3 + i];
       }
-      for (int i = lane_id(); i < S.L * 2; i += 32) M.p[i] = A.rec_p[q * A.l_max * 2 + i];
-      __syncwarp();
+      for (int i = tid(); i < S.L * 2; i += kAdjThreads) M.p[i] = A.rec_p[q * A.l_max * 2 + i];
+      __syncthreads();
       substep_adj(S, A, A.step0 + st, sb, M, it, tb);
     }
   }
-  for (int i = lane_id(); i < S.N * 3; i += 32) { gxb[i] = M.xb[i]; gvb[i] = M.vb[i]; }
-  for (int i = lane_id(); i < S.L * 2; i += 32) gpb[i] = M.pb[i];
+  for (int i = tid(); i < S.N * 3; i += kAdjThreads) { gxb[i] = M.xb[i]; gvb[i] = M.vb[i]; }
+  for (int i = tid(); i < S.L * 2; i += kAdjThreads) gpb[i] = M.pb[i];
+  // parameter adjoints: a butterfly in every warp, then the warps' sums in a fixed order
+  __shared__ float part[kAdjThreads / 32][5];
   for (int k = 0; k < 5; ++k) {
     float v = tb[k];
     for (int off = 16; off >= 1; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-    if (lane_id() == 0) A.grad[5 * s + k] += v;
+    if ((tid() & 31) == 0) part[tid() / 32][k] = v;
   }
+  __syncthreads();
+  if (tid() == 0)
+    for (int k = 0; k < 5; ++k) {
+      float v = 0.f;
+      for (int w = 0; w < kAdjThreads / 32; ++w) v += part[w][k];
+      A.grad[5 * s + k] += v;
+    }
 }
 
 // ------------------------------------------------------------------ host side
@@ -716,7 +728,7 @@ SimStatus calib_forward(CalibState& C, const SnakeParams* prm, const int* no, co
     A.step0 = step0 + (long long)c * ckpt;
     A.n_steps = std::min(ckpt, n_steps - c * ckpt);
     A.store = 0;
-    adj_forward_kernel<<<n_snakes, 32, C.smem, st>>>(A);
+    adj_forward_kernel<<<n_snakes, kAdjThreads, C.smem, st>>>(A);
     ACU(cudaGetLastError());
   }
   scatter_state_kernel<<<n_snakes, 128, 0, st>>>(pos4, vel4, press2, no, lo, n_snakes, n_max, l_max, C.x, C.v, C.p, prm);
@@ -749,12 +761,12 @@ SimStatus calib_backward(CalibState& C, const SnakeParams* prm, const int* no, c
     A.n_steps = std::min(C.ckpt, C.n_steps - c * C.ckpt);
     A.store = 1;
     A.tips = nullptr;
-    adj_forward_kernel<<<C.n_snakes, 32, C.smem, st>>>(A);
+    adj_forward_kernel<<<C.n_snakes, kAdjThreads, C.smem, st>>>(A);
     ACU(cudaGetLastError());
     A.store = 0;
     A.tips_bar = tips_bar;
     A.grad = grad;
-    adj_backward_kernel<<<C.n_snakes, 32, C.smem, st>>>(A);
+    adj_backward_kernel<<<C.n_snakes, kAdjThreads, C.smem, st>>>(A);
     ACU(cudaGetLastError());
   }
   return SIM_OK;

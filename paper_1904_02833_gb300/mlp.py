@@ -153,7 +153,7 @@ def train(mlp: WarmStartMLP, feat, target, epochs: int = 10, batch: int = 16384,
 def train_warm_start(n_snakes: int = 1024, seeds=None, rounds: int = 2, settle: int = 6,
                      steps: int = 10, tol: float = 1e-4, epochs0: int = 20, epochs: int = 10,
                      batch: int = 16384, log=None, make_batch=None, skip: float = 0.5,
-                     target_warm: int = 0):
+                     target_warm: int = 1):
     """Trains the warm-start network on data the plain solver generates.
 
     Round 0 follows cold-start trajectories; every later round follows trajectories of
