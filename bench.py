@@ -50,9 +50,9 @@ FLOP_PER_NODE_PASS = 216
 # 1,261,356-row launch of the current mlp_infer_kernel
 MLP_DRAM_BYTES_PER_ROW = (80.799232e6 + 2.060544e6) / 1261356
 # DRAM bytes per node of a split-mode launch of the 32-lane x 3-node solver kernel: ncu
-# (8.27776 MB read + 0.06784 MB written) over the 93,177 nodes that layout owns in the
+# (8.308224 MB read + 0.096 MB written) over the 93,177 nodes that layout owns in the
 # 4096-snake batch (the features it writes are consumed from L2 by the network)
-SPLIT_DRAM_BYTES_PER_NODE = (8.27776e6 + 0.06784e6) / 93177
+SPLIT_DRAM_BYTES_PER_NODE = (8.308224e6 + 0.096e6) / 93177
 # Minimal HBM bytes of one launch per node (float4 position and velocity read + written,
 # six float multipliers read + written), per link (float2 pressures read + written) and
 # per snake (96-byte parameters, offsets, residual, update count, status).
