@@ -41,7 +41,8 @@ LEARNED = dict(net_rows=1, net_every=3)
 TARGET_WARM = 1  # training targets: solves started from SKIP x the previous multipliers
 LEARNED_VARIANTS = {"all_every1": dict(net_rows=0, net_every=1), "bilateral_every1": dict(net_rows=1, net_every=1),
                     "bilateral_every2": dict(net_rows=1, net_every=2), "bilateral_every4": dict(net_rows=1, net_every=4),
-                    "all_every4": dict(net_rows=0, net_every=4)}
+                    "all_every4": dict(net_rows=0, net_every=4), "stretch_every1": dict(net_rows=2, net_every=1),
+                    "stretch_every2": dict(net_rows=2, net_every=2), "stretch_every3": dict(net_rows=2, net_every=3)}
 # Algorithmic FP32 operations of one Jacobi pass per node (segment geometry 29, stretch
 # 23, yaw 46, pitch 52, contact + friction 54, update 12; a division, square root or
 # transcendental counts as one operation).

@@ -97,9 +97,9 @@ typedef struct {
 } SimConfig;
 
 /* Row kinds the network predicts in the learned warm start: all six (stretch, yaw, pitch,
- * contact, friction x / y), or the bilateral rows only (stretch, yaw, pitch), the
- * contact and friction rows then starting from beta lambda_prev. */
-enum { SIM_NET_ROWS_ALL = 0, SIM_NET_ROWS_BILATERAL = 1 };
+ * contact, friction x / y), the bilateral rows only (stretch, yaw, pitch), or the stretch
+ * rows only; the other rows then start from beta lambda_prev. */
+enum { SIM_NET_ROWS_ALL = 0, SIM_NET_ROWS_BILATERAL = 1, SIM_NET_ROWS_STRETCH = 2 };
 
 /* Substep solvers: the Jacobi relaxation of Eq. 8 (`iters` caps its updates), or the
  * paper's Newton steps with a preconditioned conjugate residual solve of the Schur system

@@ -166,7 +166,7 @@ struct Cfg {
   int latency, law_every;        // chamber model (0 exponential, 1 Sec. V-A law), its period
   double k_i, k_d, t_p, p_s;     // Sec. V-A law: gains, deflation threshold, source pressure
   int solver, pcr_iters;         // 0 Jacobi; 1 Newton + preconditioned conjugate residual
-  int net_rows, net_every;       // learned warm start: kinds predicted (0 all, 1 bilateral), period
+  int net_rows, net_every;       // learned warm start: kinds predicted (0 all, 1 bilateral, 2 stretch), period
 };
 Cfg load_cfg(const double* c) {
   Cfg C;
@@ -671,7 +671,8 @@ double snake_step(const Snake<T>& S, const Cfg& C, long long step_index, V3<T>* 
         std::vector<double> F((size_t)N * NK * kFeat);
         row_features(S, C, X, v, lam, theta, F.data());
         for (size_t j = 0; j < lam.size(); ++j)
-          if (C.net_rows == 0 || (int)(j % NK) <= R_PITCH) y[j] = mlp_forward(mlp, &F[j * kFeat]);
+          if (C.net_rows == 0 || (int)(j % NK) <= (C.net_rows == 1 ? R_PITCH : R_STRETCH))
+            y[j] = mlp_forward(mlp, &F[j * kFeat]);
       }
       const double sc = val(S.mass) * 9.81 * h * h;
       for (size_t j = 0; j < lam.size(); ++j) lam[j] = C.beta * lam[j] + T(y[j] * sc);

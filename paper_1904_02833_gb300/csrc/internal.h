@@ -92,9 +92,9 @@ SimStatus calib_backward(CalibState& C, const SnakeParams* prm, const int* node_
 // Records the message returned by sim_last_error() on this thread.
 void set_last_error(const char* msg);
 // Enqueues the warm-start network on `feat` [rows][32] -> out [rows] (no synchronisation).
-// bilateral = 1: only the first three of every six rows (stretch, yaw, pitch of a node);
-// rows then counts those rows.
+// sel = SIM_NET_ROWS_*: all rows, the first three of every six (stretch, yaw, pitch of a
+// node) or the first of every six (stretch); rows then counts those rows.
 SimStatus mlp_forward_launch(MlpHandle* h, const void* feat, long long rows, float* out,
-                             cudaStream_t stream, int bilateral);
+                             cudaStream_t stream, int sel);
 
 }  // namespace snakesim

@@ -138,15 +138,16 @@ constexpr int kInferThreads = 256;
 // 32 (w % 4) .. +31) and takes the column half w / 4 of both epilogues, so each row's
 // 256 SiLU evaluations are split between two threads; the next tile's features are
 // loaded into registers while the current tile's MMAs run.
-// bilateral = 1: the network's row r is row 6 (r / 3) + r % 3 of feat and out (the stretch,
-// yaw and pitch rows of node r / 3 in the solver's six-rows-per-node order).
-__device__ __forceinline__ long long infer_row(long long r, int bilateral) {
-  return bilateral ? 6 * (r / 3) + r % 3 : r;
+// The rows the network runs on, in the solver's six-rows-per-node order: sel = 0 all rows;
+// sel = 1 the stretch, yaw and pitch rows (row r is row 6 (r / 3) + r % 3 of feat and out);
+// sel = 2 the stretch rows (row r is row 6 r).
+__device__ __forceinline__ long long infer_row(long long r, int sel) {
+  return sel == 1 ? 6 * (r / 3) + r % 3 : (sel == 2 ? 6 * r : r);
 }
 __global__ void __launch_bounds__(kInferThreads, 2) mlp_infer_kernel(const __nv_bfloat16* __restrict__ feat,
                                                                     long long rows, MlpDev w,
                                                                     float* __restrict__ out, int* err,
-                                                                    int bilateral) {
+                                                                    int sel) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   InferSmem& S = *reinterpret_cast<InferSmem*>(smem_raw);
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
@@ -178,7 +179,7 @@ __global__ void __launch_bounds__(kInferThreads, 2) mlp_infer_kernel(const __nv_
       const int c = t + u * kInferThreads;
       const long long r = tile * kTile + (c >> 2);
       v[u] = make_uint4(0u, 0u, 0u, 0u);
-      if (tile < ntiles && r < rows) v[u] = reinterpret_cast<const uint4*>(feat + infer_row(r, bilateral) * kInPad)[c & 3];
+      if (tile < ntiles && r < rows) v[u] = reinterpret_cast<const uint4*>(feat + infer_row(r, sel) * kInPad)[c & 3];
     }
   };
   uint4 nxt[2];
@@ -248,7 +249,7 @@ __global__ void __launch_bounds__(kInferThreads, 2) mlp_infer_kernel(const __nv_
     __syncthreads();
     tc::fence_after_sync();
     const long long r = tile * kTile + row;
-    if (half == 0 && r < rows) out[infer_row(r, bilateral)] = (y + S.part[row]) + b3;
+    if (half == 0 && r < rows) out[infer_row(r, sel)] = (y + S.part[row]) + b3;
   }
   if (!ok) {
     if (t == 0) atomicExch(err, 1);
@@ -513,7 +514,7 @@ __global__ void mlp_pack_kernel(const float* __restrict__ p, __nv_bfloat16* __re
 struct MlpHandle;
 namespace snakesim {
 SimStatus mlp_forward_launch(MlpHandle* h, const void* feat, long long rows, float* out, cudaStream_t st,
-                             int bilateral);
+                             int sel);
 }
 struct MlpHandle {
   cudaStream_t stream = nullptr;
@@ -552,12 +553,12 @@ SimStatus check_err(MlpHandle* h) {
 }  // namespace
 
 SimStatus snakesim::mlp_forward_launch(MlpHandle* h, const void* feat, long long rows, float* out,
-                                       cudaStream_t st, int bilateral) {
+                                       cudaStream_t st, int sel) {
   if (rows <= 0) return SIM_OK;
   const long long tiles = (rows + kTile - 1) / kTile;
   const int grid = (int)std::min<long long>(tiles, 2LL * h->sms);
   mlp_infer_kernel<<<grid, kInferThreads, sizeof(InferSmem), st>>>((const __nv_bfloat16*)feat, rows, dev_of(h),
-                                                                  out, h->err, bilateral);
+                                                                  out, h->err, sel);
   MCU(cudaGetLastError());
   return SIM_OK;
 }

@@ -323,9 +323,8 @@ SimStatus validate_cfg(const SimConfig* c) {
     return fail(SIM_EINVAL, "invalid config: solver must be SIM_SOLVER_JACOBI or SIM_SOLVER_NEWTON_PCR");
   if (c->solver == SIM_SOLVER_NEWTON_PCR && (c->contact != 0 || c->pcr_iters < 1))
     return fail(SIM_EINVAL, "the Newton + PCR solver needs contact = 0 and pcr_iters >= 1");
-  if ((c->net_rows != SIM_NET_ROWS_ALL && c->net_rows != SIM_NET_ROWS_BILATERAL) || c->net_every < 0)
-    return fail(SIM_EINVAL, "invalid config: net_rows must be SIM_NET_ROWS_ALL or SIM_NET_ROWS_BILATERAL, "
-                            "net_every >= 0");
+  if (c->net_rows < SIM_NET_ROWS_ALL || c->net_rows > SIM_NET_ROWS_STRETCH || c->net_every < 0)
+    return fail(SIM_EINVAL, "invalid config: net_rows must be one of SIM_NET_ROWS_*, net_every >= 0");
   if (c->latency != SIM_LATENCY_EXP && c->latency != SIM_LATENCY_LAW)
     return fail(SIM_EINVAL, "invalid config: latency must be SIM_LATENCY_EXP or SIM_LATENCY_LAW");
   if (c->latency == SIM_LATENCY_LAW &&
@@ -649,9 +648,9 @@ SimStatus launch_args(SimHandle* h, const SolverArgs& A, cudaStream_t st) {
 SimStatus launch_net(SimHandle* h, int l, cudaStream_t s) {
   const long long r0 = 6LL * h->lay_fnode[l], r1 = 6LL * h->lay_fnode[l + 1];
   if (r1 <= r0) return SIM_OK;
-  const int bilateral = h->cfg.net_rows == SIM_NET_ROWS_BILATERAL;
-  SimStatus r = mlp_forward_launch(h->mlp, h->feat + r0 * 32, bilateral ? (r1 - r0) / 2 : r1 - r0,
-                                   h->lam0 + r0, s, bilateral);
+  const int sel = h->cfg.net_rows;
+  const long long rows = sel == SIM_NET_ROWS_BILATERAL ? (r1 - r0) / 2 : (sel == SIM_NET_ROWS_STRETCH ? (r1 - r0) / 6 : r1 - r0);
+  SimStatus r = mlp_forward_launch(h->mlp, h->feat + r0 * 32, rows, h->lam0 + r0, s, sel);
   h->launches += 1;
   return r;
 }

@@ -340,19 +340,21 @@ __device__ __forceinline__ float row_pass(const SnakeK& S, const SolverArgs& A, 
     fromR[d] = __shfl_down_sync(kFull, accL[d], 1, G);  // right lane's rows -> my last node
     fromL[d] = __shfl_up_sync(kFull, accR[d], 1, G);    // left lane's rows -> my first node
   }
-  if (live && !stop) {
+  // update, by selects: a node slot beyond the snake or a group that stops keeps its state
+  const bool upd = live && !stop;
 #pragma unroll
-    for (int j = 0; j < NPL; ++j) {
-      const int i = i0 + j;
-      if (i >= S.N) continue;
-      float ax = acc[j][0], ay = acc[j][1], az = acc[j][2];
-      if (j == 0 && q > 0) { ax += fromL[0]; ay += fromL[1]; az += fromL[2]; }
-      if (j == NPL - 1 && q < G - 1) { ax += fromR[0]; ay += fromR[1]; az += fromR[2]; }
-      const float wi = (i < S.nfix) ? 0.f : S.inv_m;
-      dx[j][0] += wi * ax; dx[j][1] += wi * ay; dx[j][2] += wi * az;
+  for (int j = 0; j < NPL; ++j) {
+    const int i = i0 + j;
+    float ax = acc[j][0], ay = acc[j][1], az = acc[j][2];
+    if (j == 0 && q > 0) { ax += fromL[0]; ay += fromL[1]; az += fromL[2]; }
+    if (j == NPL - 1 && q < G - 1) { ax += fromR[0]; ay += fromR[1]; az += fromR[2]; }
+    const bool on = upd && i < S.N;
+    const float wi = (i < S.nfix) ? 0.f : S.inv_m;
+    dx[j][0] = on ? dx[j][0] + wi * ax : dx[j][0];
+    dx[j][1] = on ? dx[j][1] + wi * ay : dx[j][1];
+    dx[j][2] = on ? dx[j][2] + wi * az : dx[j][2];
 #pragma unroll
-      for (int k = 0; k < 6; ++k) lam[j][k] = WARM ? dl[j][k] : lam[j][k] + dl[j][k];
-    }
+    for (int k = 0; k < 6; ++k) lam[j][k] = on ? (WARM ? dl[j][k] : lam[j][k] + dl[j][k]) : lam[j][k];
   }
   return r;
 }
@@ -771,7 +773,8 @@ __device__ void run_group(const SolverArgs& A, int snake, bool valid, float* sme
 #pragma unroll
         for (int k = 0; k < 6; ++k) {
           float l = A.beta * lam[j][k];
-          if (A.warm == 2 && net && A.lam0 && valid && i < S.N && (A.net_rows == SIM_NET_ROWS_ALL || k < 3))
+          if (A.warm == 2 && net && A.lam0 && valid && i < S.N &&
+              (A.net_rows == SIM_NET_ROWS_ALL || k < (A.net_rows == SIM_NET_ROWS_BILATERAL ? 3 : 1)))
             l += A.lam0[(size_t)(S.fb + i) * 6 + k] * sc;
           lam[j][k] = l;
         }
@@ -827,14 +830,13 @@ __device__ void run_group(const SolverArgs& A, int snake, bool valid, float* sme
     }
   } else {
     if (A.sub > 0 && valid && q == 0) { rmax = A.resid[snake]; itot = A.iters[snake]; }
+    // the substep begun by the previous launch, then the rest of the span in full (one
+    // call site, so that the kernel carries one copy of the pass)
     int next = A.sub + 1;
-    if (A.sub >= 0) {
-      // the substep begun by the previous launch, then the rest of the span in full
-      finish_substep(rmax, itot, A.sub % A.net_every == 0);
-      for (; next < A.sub + A.span && next < A.n_sub; ++next) {
-        begin_substep(step0, next);
-        finish_substep(rmax, itot, next % A.net_every == 0);
-      }
+    for (int t = A.sub; t >= 0 && t < A.sub + A.span && t < A.n_sub; ++t) {
+      if (t > A.sub) begin_substep(step0, t);
+      finish_substep(rmax, itot, t % A.net_every == 0);
+      next = t + 1;
     }
     if (next < A.n_sub) {
       begin_substep(step0, next);

@@ -143,7 +143,7 @@ def test_split_stepping_matches_fused_stepping():
         assert np.abs(sa["vel"] - sb["vel"]).max() <= tol_x / h
 
 
-@pytest.mark.parametrize("net_rows,net_every", [(0, 1), (1, 1), (0, 4), (1, 7), (0, 20)])
+@pytest.mark.parametrize("net_rows,net_every", [(0, 1), (1, 1), (0, 4), (1, 7), (0, 20), (2, 1), (2, 3)])
 def test_learned_mode_matches_oracle(net_rows, net_every):
     """Same network parameters on both sides; fixed iteration count; the network on all
     row kinds or the bilateral ones, at every substep or every net_every-th (the launches

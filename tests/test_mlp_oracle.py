@@ -125,13 +125,14 @@ def test_training_target_inverts_the_learned_warm_start(beta):
     assert np.array_equal(F[:, :6].sum(1), np.ones(len(F)))
 
 
-@pytest.mark.parametrize("net_rows,net_every", [(0, 1), (0, 2), (1, 2), (1, 1)])
+@pytest.mark.parametrize("net_rows,net_every", [(0, 1), (0, 2), (1, 2), (1, 1), (2, 1), (2, 3)])
 def test_learned_warm_start_schedule_closed_form(net_rows, net_every):
     """Which substeps and row kinds take the network's prediction.  With no updates
     applied (cap 0) a substep ends on its warm start, so with a network of constant output
     c the multipliers after three substeps are, per row, b^3 l_init plus c m g h^2 times
     b^2 (substep 0), b (substep 1) and 1 (substep 2) for each substep s with
-    s % net_every == 0, on the predicted kinds only (all six, or stretch, yaw, pitch)."""
+    s % net_every == 0, on the predicted kinds only (all six; stretch, yaw, pitch; or
+    stretch)."""
     w = W.batched(n=3, seed=13, links=(1, 3))
     s = W.solver_settings(iters=10, n_sub=3)
     o = oracle.OracleSim(w, s)
@@ -145,7 +146,7 @@ def test_learned_warm_start_schedule_closed_form(net_rows, net_every):
     h = s["dt"] / 3
     sc = np.repeat(w["mass"] * 9.81 * h * h, W.n_nodes(w))[:, None]
     weight = sum(b ** (2 - k) for k in range(3) if k % net_every == 0)
-    pred = np.ones((1, 6)) if net_rows == 0 else np.array([[1, 1, 1, 0, 0, 0]])
+    pred = {0: np.ones((1, 6)), 1: np.array([[1, 1, 1, 0, 0, 0]]), 2: np.array([[1, 0, 0, 0, 0, 0]])}[net_rows]
     expect = b ** 3 * lam0 + c * weight * sc * pred
     # rows that do not exist stay zero (the chain's ends)
     F = o.features()

@@ -57,7 +57,8 @@ def solver_settings(dt=1.0 / 60.0, n_sub=20, iters=10, tol=0.0, omega=1.0 / 3.0,
     Jacobi relaxation, `iters` capping its passes; 1 = Newton steps each with `pcr_iters`
     preconditioned conjugate residual iterations, Sec. IV-D, `iters` capping the
     matrix-vector products; contact-free only); for the learned warm start, the row kinds
-    the network predicts (net_rows 0 = all six, 1 = stretch, yaw and pitch only) and every
+    the network predicts (net_rows 0 = all six, 1 = stretch, yaw and pitch only, 2 = stretch
+    only) and every
     how many substeps it runs (net_every; the substeps in between start from beta x the
     previous multipliers)."""
     return dict(dt=float(dt), n_sub=int(n_sub), iters=int(iters), tol=float(tol),
