@@ -265,3 +265,45 @@ def test_snapshot_branch_inside_a_split_step_is_invisible():
         g.close()
     for k in runs[0]:
         assert np.array_equal(runs[0][k], runs[1][k]), k
+
+
+def test_training_rows_and_learned_options_reject_bad_arguments():
+    """sim_training_rows refuses a call outside a begun substep, an output smaller than the
+    row count and a misaligned feature buffer, and reports the count when asked; the
+    configuration refuses unknown row kinds and a negative network period."""
+    import ctypes
+    from paper_1904_02833_gb300 import _native as N
+    from paper_1904_02833_gb300.sim import SnakeSim
+    lib = N.load()
+    w = W.batched(n=6, seed=36, links=(1, 3))
+    s = W.solver_settings(iters=10)
+    g = SnakeSim(w, s)
+    lam = g.lam().clone()
+    n = ctypes.c_int64(-1)
+    P = ctypes.c_void_p
+    assert lib.sim_training_rows(g.h, None, None, 0.5, None, None, 0, ctypes.byref(n)) == N.SIM_EINVAL
+    g.split_begin()
+    # the autotuner would time whole env-steps: refused while one is split
+    assert lib.sim_autotune(g.h, 1) == N.SIM_EINVAL
+    assert lib.sim_training_rows(g.h, None, None, 0.5, None, None, 0, ctypes.byref(n)) == N.SIM_OK
+    rows = n.value
+    nodes = W.n_nodes(w)
+    assert rows == int(sum(N_ - 1 + 2 * (N_ - 2) + 3 * N_ for N_ in nodes))
+    feat = torch.empty(rows + 1, 32, dtype=torch.bfloat16, device="cuda")
+    tgt = torch.empty(rows, device="cuda")
+    lp = P(lam.data_ptr())
+    assert lib.sim_training_rows(g.h, lp, lp, 0.5, P(feat.data_ptr()), P(tgt.data_ptr()), rows - 1,
+                                 ctypes.byref(n)) == N.SIM_EINVAL
+    assert lib.sim_training_rows(g.h, lp, lp, 0.5, P(feat.data_ptr() + 8), P(tgt.data_ptr()), rows,
+                                 ctypes.byref(n)) == N.SIM_EINVAL
+    assert b"aligned" in lib.sim_last_error()
+    assert lib.sim_training_rows(g.h, lp, lp, 1.5, P(feat.data_ptr()), P(tgt.data_ptr()), rows,
+                                 ctypes.byref(n)) == N.SIM_EINVAL
+    assert lib.sim_training_rows(g.h, lp, lp, 0.5, P(feat.data_ptr()), P(tgt.data_ptr()), rows,
+                                 ctypes.byref(n)) == N.SIM_OK
+    torch.cuda.synchronize()
+    g.split_finish()
+    for bad in (dict(net_rows=3), dict(net_rows=-1), dict(net_every=-2)):
+        with pytest.raises(N.SimError):
+            g.set_config(**dict(s, **bad))
+    g.close()
