@@ -32,6 +32,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include <cuda_bf16.h>
 
 #include "internal.h"
@@ -272,8 +274,20 @@ __device__ __forceinline__ float row_pass(const SnakeK& S, const SolverArgs& A, 
       acc[j][0] += g1x * d; acc[j][1] += g1y * d; acc[j][2] += g1z * d;
       tr[0] += g2x * d; tr[1] += g2y * d; tr[2] += g2z * d;
     }
-    // ---- ground contact (Eq. 7, z - r >= 0) and Coulomb friction pair
-    {
+    sp = sc;
+  }
+  // ---- ground contact (Eq. 7, z - r >= 0) and Coulomb friction pair of every node slot.
+  // Their residual terms decide nothing in a pass where every group's bilateral terms
+  // already exceed the tolerance (the group cannot stop) and the cap is not reached, so
+  // they are evaluated only when some group's could decide it (warp-uniform choice
+  // between two compiled forms of the loop); the updates are the same either way.
+  auto contact_rows = [&](auto with_residual) {
+    constexpr bool RES = decltype(with_residual)::value;
+#pragma unroll
+    for (int j = 0; j < NPL; ++j) {
+      const int i = i0 + j;
+      const bool act = live && i < S.N;
+      const float wi = (i < S.nfix) ? 0.f : S.inv_m;
       const bool on = act && A.contact && wi > 0.f;
       const float ln = lam[j][3];
       const float cn = (xs[j][2] - S.radius) + dx[j][2];
@@ -293,14 +307,16 @@ __device__ __forceinline__ float row_pass(const SnakeK& S, const SolverArgs& A, 
           const float ex = bx0 - ax0, ey = by0 - ay0, en2 = ex * ex + ey * ey;
           if (en2 > 0.f) { const float ie = rsqrtf(en2); bx = ex * ie; by = ey * ie; }
         }
-        // residuals: Fischer-Burmeister on (c_n, w lambda_n); natural map of the cone
-        const float b = wi * ln;
-        r = fmaxf(r, on ? fabsf(cn + b - sqrtf(cn * cn + b * b)) : 0.f);
-        const float ax = wi * lam[j][4], ay = wi * lam[j][5];
-        float px = ax - ux, py = ay - uy;
-        friction_limit<ANISO>(S, bx, by, wi * ln, px, py);
-        // squared friction residual; one square root per pass for the whole lane
-        q2 = fmaxf(q2, on ? (ax - px) * (ax - px) + (ay - py) * (ay - py) : 0.f);
+        if constexpr (RES) {
+          // residuals: Fischer-Burmeister on (c_n, w lambda_n); natural map of the cone
+          const float b = wi * ln;
+          r = fmaxf(r, on ? fabsf(cn + b - sqrtf(cn * cn + b * b)) : 0.f);
+          const float ax = wi * lam[j][4], ay = wi * lam[j][5];
+          float px = ax - ux, py = ay - uy;
+          friction_limit<ANISO>(S, bx, by, wi * ln, px, py);
+          // squared friction residual; one square root per pass for the whole lane
+          q2 = fmaxf(q2, on ? (ax - px) * (ax - px) + (ay - py) * (ay - py) : 0.f);
+        }
         // contact: lambda_n <- max(0, lambda_n + omega (-c_n / w))
         const float nl = fmaxf(0.f, ln - S.om_m * cn);
         dn = nl - ln;
@@ -317,8 +333,19 @@ __device__ __forceinline__ float row_pass(const SnakeK& S, const SolverArgs& A, 
       acc[j][0] += fx;
       acc[j][1] += fy;
     }
-    sp = sc;
+  };
+  bool cf_residual = true;
+  if (!WARM) {
+    // a group could stop only if none of its lanes has a bilateral term over the
+    // tolerance (a non-finite term counts as not over, so that it reaches the residual)
+    const float rb = r * S.inv_L0;
+    const unsigned ln_ = threadIdx.x & 31u;
+    const unsigned gm = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (ln_ & ~(unsigned)(G - 1)));
+    const unsigned over_b = __ballot_sync(kFull, rb > A.tol);
+    cf_residual = __any_sync(kFull, live && (over_b & gm) == 0u) || kiter >= A.K;
   }
+  if (cf_residual) contact_rows(std::true_type{});
+  else contact_rows(std::false_type{});
   if (!WARM) {
     // every term is a length: one scaling by 1 / L0 (monotone, so the max is the same)
     r = fmaxf(r, sqrtf(q2)) * S.inv_L0;
