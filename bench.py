@@ -47,13 +47,13 @@ LEARNED_VARIANTS = {"all_every1": dict(net_rows=0, net_every=1), "bilateral_ever
 # 23, yaw 46, pitch 52, contact + friction 54, update 12; a division, square root or
 # transcendental counts as one operation).
 FLOP_PER_NODE_PASS = 216
-# DRAM bytes per row of the network kernel: ncu (80.80 MB read + 2.06 MB written) over a
+# DRAM bytes per row of the network kernel: ncu (80.80 MB read + 1.98 MB written) over a
 # 1,261,356-row launch of the current mlp_infer_kernel
-MLP_DRAM_BYTES_PER_ROW = (80.799232e6 + 2.060544e6) / 1261356
+MLP_DRAM_BYTES_PER_ROW = (80.797440e6 + 1.975808e6) / 1261356
 # DRAM bytes per node of a split-mode launch of the 32-lane x 3-node solver kernel: ncu
-# (8.308224 MB read + 0.096 MB written) over the 93,177 nodes that layout owns in the
+# (8.282624 MB read + 0.077312 MB written) over the 93,177 nodes that layout owns in the
 # 4096-snake batch (the features it writes are consumed from L2 by the network)
-SPLIT_DRAM_BYTES_PER_NODE = (8.308224e6 + 0.096e6) / 93177
+SPLIT_DRAM_BYTES_PER_NODE = (8.282624e6 + 0.077312e6) / 93177
 # Minimal HBM bytes of one launch per node (float4 position and velocity read + written,
 # six float multipliers read + written), per link (float2 pressures read + written) and
 # per snake (96-byte parameters, offsets, residual, update count, status).
@@ -274,10 +274,12 @@ def run_gpu(args):
     reps = 10
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("network_alone")
     for a, b in evs:
         a.record(stream)
         net.lib.mlp_forward(net.h, ctypes.c_void_p(feat.data_ptr()), rows, ctypes.c_void_p(out.data_ptr()))
         b.record(stream)
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     mlp_ms = float(np.median([a.elapsed_time(b) for a, b in evs]))
 

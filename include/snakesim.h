@@ -314,6 +314,14 @@ SimStatus mlp_train_step(MlpHandle* m, const void* feat, const float* target, in
                          float lr, float* loss);
 /* Synchronises and reports a timed-out tensor-core wait of earlier asynchronous calls. */
 SimStatus mlp_check(MlpHandle* m);
+/* Self-test of the bounded waits the network kernels use on tensor-core completions (no
+ * counterpart in the paper): on `stream` (cudaStream_t) one block allocates tensor memory,
+ * waits at most `polls` polls on a barrier that nothing arrives on, records that the wait
+ * ran out and frees its tensor memory before returning, as the network kernels do when a
+ * completion never arrives (they then report SIM_ECUDA).  *timed_out (host) receives 1
+ * when the wait ran out, the expected result; the device stays usable.  Synchronises
+ * `stream`.  Errors: SIM_EINVAL (polls < 1, null pointer), SIM_ECUDA. */
+SimStatus mlp_wait_selftest(uint32_t polls, void* stream, int32_t* timed_out);
 SimStatus mlp_destroy(MlpHandle* m);
 
 /* Allocation-free forward pass, for callers that cannot allocate device memory (a

@@ -110,6 +110,7 @@ SIGNATURES = {
     "mlp_grad": [H, P, P, ctypes.c_int64, ctypes.c_float, P, P],
     "mlp_train_step": [H, P, P, ctypes.c_int64, ctypes.c_float, P],
     "mlp_check": [H],
+    "mlp_wait_selftest": [ctypes.c_uint32, P, ctypes.POINTER(ctypes.c_int32)],
     "mlp_destroy": [H],
     "mlp_forward_noalloc": [P, ctypes.c_int32, P, ctypes.c_int64, P, P],
     "fem_create": [ctypes.POINTER(FemConfig), ctypes.POINTER(FemMesh), ctypes.c_int,

@@ -260,6 +260,26 @@ __global__ void __launch_bounds__(kInferThreads, 2) mlp_infer_kernel(const __nv_
   if (warp == 0) tc::tmem_dealloc(tmem, 256);
 }
 
+// Self-test of the bounded tensor-core waits: one block allocates tensor memory, waits
+// with a bound of `polls` on an mbarrier that nothing arrives on (so the wait runs out, as
+// a lost MMA completion would make the network kernels' waits run out), records the
+// timeout in *err and frees its tensor memory before returning, as those kernels do.
+__global__ void __launch_bounds__(128) mlp_wait_selftest_kernel(uint32_t polls, int* err) {
+  __shared__ uint64_t mbar;
+  __shared__ uint32_t tmem_addr;
+  const int t = threadIdx.x, warp = t >> 5;
+  if (warp == 0) tc::tmem_alloc(&tmem_addr, 32);
+  if (t == 0) tc::mbar_init(&mbar, 1);
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  if (__syncthreads_or(!tc::mbar_wait(&mbar, 0, polls)) && t == 0) atomicExch(err, 1);
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem_addr, 32);
+}
+
 namespace {
 
 struct TrainSmem {
@@ -670,6 +690,25 @@ SimStatus mlp_train_step(MlpHandle* h, const void* feat, const float* target, in
 SimStatus mlp_check(MlpHandle* h) {
   if (!h) return mfail(SIM_EINVAL, "null handle");
   return check_err(h);
+}
+
+SimStatus mlp_wait_selftest(uint32_t polls, void* stream, int32_t* timed_out) {
+  if (polls < 1 || !timed_out) return mfail(SIM_EINVAL, "polls >= 1 and a result pointer");
+  cudaStream_t st = (cudaStream_t)stream;
+  int* flag = nullptr;
+  MCU(cudaMalloc(&flag, sizeof(int)));
+  int e = 0;
+  cudaError_t c = cudaMemsetAsync(flag, 0, sizeof(int), st);
+  if (c == cudaSuccess) {
+    mlp_wait_selftest_kernel<<<1, 128, 0, st>>>(polls, flag);
+    c = cudaGetLastError();
+  }
+  if (c == cudaSuccess) c = cudaMemcpyAsync(&e, flag, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (c == cudaSuccess) c = cudaStreamSynchronize(st);
+  cudaFree(flag);
+  if (c != cudaSuccess) return mfail(SIM_ECUDA, std::string("mlp_wait_selftest: ") + cudaGetErrorString(c));
+  *timed_out = e;
+  return SIM_OK;
 }
 
 SimStatus mlp_destroy(MlpHandle* h) {

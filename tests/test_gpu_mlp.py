@@ -307,3 +307,24 @@ def test_training_rows_and_learned_options_reject_bad_arguments():
         with pytest.raises(N.SimError):
             g.set_config(**dict(s, **bad))
     g.close()
+
+
+def test_bounded_tensor_core_wait_times_out_and_leaves_the_device_usable():
+    """A tensor-core completion that never arrives: the bounded wait runs out, the block
+    records it and frees its tensor memory; the status reaches the host, and the network
+    kernels (which allocate all of an SM's tensor memory between two blocks) run and agree
+    with the oracle afterwards."""
+    import ctypes
+    from paper_1904_02833_gb300 import _native as N
+    lib = N.load()
+    st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    for _ in range(3):
+        out = ctypes.c_int32(-1)
+        assert lib.mlp_wait_selftest(4096, st, ctypes.byref(out)) == N.SIM_OK
+        assert out.value == 1
+    assert lib.mlp_wait_selftest(0, st, ctypes.byref(ctypes.c_int32())) == N.SIM_EINVAL
+    p = M.init_params(9)
+    f = feats(4000, 3)
+    y = mlp(p).forward(to_dev(f)).cpu().numpy()
+    ref = oracle.mlp_forward(p, M.bf16(f))
+    assert np.abs(y - ref).max() <= 5e-3 * max(np.abs(ref).mean() + 1e-3, np.abs(ref).max())
