@@ -451,3 +451,54 @@ def test_full_size_sampled_parity():
         xg = st["pos"][g.node_off[k]:g.node_off[k + 1]]
         xo = o.x[o.node_off[j]:o.node_off[j + 1]]
         assert np.abs(xg - xo).max() <= 1e-5 * np.abs(xo).max(), k
+
+
+class _Rows:
+    """The host state of selected snakes of a GPU batch, in the shape compare() reads."""
+
+    def __init__(self, st, g, sel):
+        nodes = np.concatenate([np.arange(g.node_off[k], g.node_off[k + 1]) for k in sel])
+        links = np.concatenate([np.arange(g.link_off[k], g.link_off[k + 1]) for k in sel])
+        self.st = {"pos": st["pos"][nodes], "vel": st["vel"][nodes], "press": st["press"][links],
+                   "resid": st["resid"][sel], "iters": st["iters"][sel]}
+
+    def state_host(self):
+        return self.st
+
+
+def test_benchmark_configuration_sampled_parity():
+    """The benchmark's launch configuration: the 16384-snake evaluation batch, lane layouts
+    autotuned per mode, Jacobi to residual 1e-4; plain, previous-multiplier and learned
+    (network on the bilateral rows at every third substep, spans of three substeps per
+    launch) env-steps from one state; 12 sampled snakes recomputed by the oracle alone
+    (snakes are independent).  To a tolerance FP32 and FP64 may stop a substep a few
+    updates apart, hence the velocity floor and the count bound."""
+    from oracle import mlp_oracle as M
+    from paper_1904_02833_gb300.mlp import WarmStartMLP
+    import bench
+    w = bench.eval_batch(1)
+    n = len(w["n_links"])
+    s = W.solver_settings(iters=5000, tol=1e-4)
+    g = Sim(w, s)
+    g.step(1)
+    rng = np.random.default_rng(5)
+    sel = np.sort(rng.choice(n, 12, replace=False))
+    o = oracle.OracleSim(W.subset(w, sel), s)
+    o.step(1)
+    p = M.init_params(11) * 0.5
+    net = WarmStartMLP(p)
+    g.set_mlp(net)
+    for cfg in (dict(warm=0), dict(warm=1, beta=0.5), dict(warm=2, beta=0.5, net_rows=1, net_every=3)):
+        g.set_config(**cfg)
+        o.set_cfg(**cfg)
+        g.autotune(1)
+        assert all(G * npl >= N for N, (G, npl) in ((int(N), g.layout(int(N))) for N in np.unique(W.n_nodes(w))))
+        g.step(1, graph=True)
+        o.step(1, mlp=p)
+        st = g.state_host()
+        sub = _Rows(st, g, sel)
+        compare(sub, o, vel_floor=5e-3)
+        assert (sub.st["resid"] <= 1e-4).all() and (o.resid <= 1e-4).all()
+        assert (np.abs(sub.st["iters"] - o.iters) <= np.maximum(0.05 * o.iters, 20)).all(), (cfg, sub.st["iters"], o.iters)
+    g.close()
+    net.close()
