@@ -469,8 +469,8 @@ class _Rows:
 def test_benchmark_configuration_sampled_parity():
     """The benchmark's launch configuration: the 16384-snake evaluation batch, lane layouts
     autotuned per mode, Jacobi to residual 1e-4; plain, previous-multiplier and learned
-    (network on the bilateral rows at every third substep, spans of three substeps per
-    launch) env-steps from one state; 12 sampled snakes recomputed by the oracle alone
+    (the benchmark's own learned settings: the network on the bilateral rows at every
+    second substep, spans of two substeps per launch) env-steps from one state; 12 sampled snakes recomputed by the oracle alone
     (snakes are independent).  To a tolerance FP32 and FP64 may stop a substep a few
     updates apart, hence the velocity floor and the count bound."""
     from oracle import mlp_oracle as M
@@ -488,7 +488,7 @@ def test_benchmark_configuration_sampled_parity():
     p = M.init_params(11) * 0.5
     net = WarmStartMLP(p)
     g.set_mlp(net)
-    for cfg in (dict(warm=0), dict(warm=1, beta=0.5), dict(warm=2, beta=0.5, net_rows=1, net_every=3)):
+    for cfg in (dict(warm=0), dict(warm=1, beta=0.5), dict(warm=2, beta=bench.SKIP, **bench.LEARNED)):
         g.set_config(**cfg)
         o.set_cfg(**cfg)
         g.autotune(1)
