@@ -51,9 +51,10 @@ FLOP_PER_NODE_PASS = 216
 # 1,261,356-row launch of the current mlp_infer_kernel
 MLP_DRAM_BYTES_PER_ROW = (80.797440e6 + 1.975808e6) / 1261356
 # DRAM bytes per node of a split-mode launch of the 32-lane x 3-node solver kernel: ncu
-# (8.282624 MB read + 0.077312 MB written) over the 93,177 nodes that layout owns in the
-# 4096-snake batch (the features it writes are consumed from L2 by the network)
-SPLIT_DRAM_BYTES_PER_NODE = (8.282624e6 + 0.077312e6) / 93177
+# (8.283136 MB read + 0.097024 MB written, a launch of two substeps) over the 93,177
+# nodes that layout owns in the 4096-snake batch (the features it writes are consumed
+# from L2 by the network)
+SPLIT_DRAM_BYTES_PER_NODE = (8.283136e6 + 0.097024e6) / 93177
 # Minimal HBM bytes of one launch per node (float4 position and velocity read + written,
 # six float multipliers read + written), per link (float2 pressures read + written) and
 # per snake (96-byte parameters, offsets, residual, update count, status).
@@ -193,7 +194,8 @@ def run_gpu(args):
         from paper_1904_02833_gb300.mlp import WarmStartMLP
         net, record = WarmStartMLP(np.load(args.load_net)), [{"loaded": args.load_net}]
     else:
-        net, record = train_warm_start(n_snakes=2048, rounds=2, skip=SKIP, target_warm=args.target_warm)
+        net, record = train_warm_start(n_snakes=2048, rounds=2, skip=SKIP, target_warm=args.target_warm,
+                                       deploy=LEARNED if args.train_schedule == "deploy" else None)
     if args.save_net:
         np.save(args.save_net, net.params())
     t_train = time.perf_counter() - t_train
@@ -377,7 +379,8 @@ def run_gpu(args):
             "data": "synthetic",
             "mode": "learned warm start (network trained on the plain solver's data, disjoint seeds; "
                     "bilateral rows, every 2nd substep)",
-            "learned_config": dict(LEARNED, beta=SKIP, target_warm=TARGET_WARM),
+            "learned_config": dict(LEARNED, beta=SKIP, target_warm=args.target_warm,
+                                   train_schedule=args.train_schedule),
             "previous_value": modes_out["previous"]["value"],
             "learned_vs_previous": value / modes_out["previous"]["value"],
             "plain_value": modes_out["plain"]["value"],
@@ -798,6 +801,9 @@ def main():
                          "1 beta x the previous multipliers")
     ap.add_argument("--no-learned-variants", action="store_true",
                     help="time only the headline learned configuration (not its variants)")
+    ap.add_argument("--train-schedule", default="all", choices=["all", "deploy"],
+                    help="row kinds and period of the network on the learned training "
+                         "trajectories: every row and substep, or the metric's learned configuration")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default lane layouts instead of timing them per mode (sim_autotune)")
     ap.add_argument("--no-configs", action="store_true",

@@ -153,7 +153,7 @@ def train(mlp: WarmStartMLP, feat, target, epochs: int = 10, batch: int = 16384,
 def train_warm_start(n_snakes: int = 1024, seeds=None, rounds: int = 2, settle: int = 6,
                      steps: int = 10, tol: float = 1e-4, epochs0: int = 20, epochs: int = 10,
                      batch: int = 16384, log=None, make_batch=None, skip: float = 0.5,
-                     target_warm: int = 1):
+                     target_warm: int = 1, deploy: dict | None = None):
     """Trains the warm-start network on data the plain solver generates.
 
     Round 0 follows cold-start trajectories; every later round follows trajectories of
@@ -162,8 +162,11 @@ def train_warm_start(n_snakes: int = 1024, seeds=None, rounds: int = 2, settle: 
     multipliers the plain solver reaches at `tol` from the same start (cold, or from
     `skip` times the previous multipliers with target_warm = 1), minus `skip` times the
     previous multipliers (the learned warm start adds the network's output to the
-    previous multipliers weighted by beta = skip).  All simulation and all
-    training run in the library's kernels.  Returns the network and a record of the
+    previous multipliers weighted by beta = skip).  `deploy` (net_rows, net_every) sets
+    the row kinds and period the learned trajectories use the network on, and the
+    logged substeps are then network substeps, so that the previous multipliers in the
+    data come from the schedule the network will be deployed with.  All simulation and
+    all training run in the library's kernels.  Returns the network and a record of the
     rounds."""
     import workloads as W  # seeded parameter generator (no simulation arithmetic)
     from .sim import SnakeSim
@@ -172,15 +175,21 @@ def train_warm_start(n_snakes: int = 1024, seeds=None, rounds: int = 2, settle: 
     seeds = list(seeds) if seeds is not None else W.training_seeds(rounds + 2)
     net = WarmStartMLP()
     feats, targets, record = [], [], []
+    deploy = dict(deploy or {})
+    every = int(deploy.get("net_every", 1))
 
     def gather(seed, learned):
         sim = SnakeSim(make_batch(n_snakes, seed), W.solver_settings(iters=5000, tol=tol, warm=0))
         sim.step(settle)
         if learned:
             sim.set_mlp(net)
-            sim.set_config(warm=2, beta=skip)
+            sim.set_config(warm=2, beta=skip, **deploy)
             sim.step(2)
-        f, t = collect(sim, steps, substeps=(0, 7, 14), every=2, target_tol=tol, skip=skip,
+        logged = (0, 7, 14)
+        if learned:  # the network substeps nearest to those
+            last = (sim.settings["n_sub"] - 1) // every * every
+            logged = tuple(sorted({min(round(s / every) * every, last) for s in logged}))
+        f, t = collect(sim, steps, substeps=logged, every=2, target_tol=tol, skip=skip,
                        target_warm=target_warm)
         sim.close()
         return f, t
