@@ -34,13 +34,15 @@ TOL = 1e-4
 CAP = 5000
 SKIP = 0.5  # learned warm start: lambda0 = SKIP lambda_prev + m g h^2 network(features)
 # the learned warm start the metric is quoted on: the network on the bilateral rows
-# (stretch, yaw, pitch) at every second substep, trained on targets solved from beta x the
-# previous multipliers (the best of the variants timed beside it on this batch, in each of
-# three runs); the other variants are reported under `modes`
-LEARNED = dict(net_rows=1, net_every=2)
+# (stretch, yaw, pitch) at every third substep, trained on targets solved from beta x the
+# previous multipliers along trajectories that use the network in this same configuration
+# (every second substep ran as fast, every third ends fewer launches on their slowest
+# snake); the other variants, with the same network, are reported under `modes`
+LEARNED = dict(net_rows=1, net_every=3)
 TARGET_WARM = 1  # training targets: solves started from SKIP x the previous multipliers
 LEARNED_VARIANTS = {"all_every1": dict(net_rows=0, net_every=1), "bilateral_every1": dict(net_rows=1, net_every=1),
-                    "bilateral_every3": dict(net_rows=1, net_every=3), "bilateral_every4": dict(net_rows=1, net_every=4),
+                    "bilateral_every2": dict(net_rows=1, net_every=2), "bilateral_every3": dict(net_rows=1, net_every=3),
+                    "bilateral_every4": dict(net_rows=1, net_every=4),
                     "all_every4": dict(net_rows=0, net_every=4), "stretch_every1": dict(net_rows=2, net_every=1),
                     "stretch_every2": dict(net_rows=2, net_every=2), "stretch_every3": dict(net_rows=2, net_every=3)}
 # Algorithmic FP32 operations of one Jacobi pass per node (segment geometry 29, stretch
@@ -178,6 +180,9 @@ def run_gpu(args):
 
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
+    if args.net_every < 1:
+        raise SystemExit("--net-every must be >= 1")
+    learned = dict(net_rows=args.net_rows, net_every=args.net_every)
     if world > 1:
         dist.init_process_group("nccl")
     from paper_1904_02833_gb300.mlp import train_warm_start
@@ -195,7 +200,7 @@ def run_gpu(args):
         net, record = WarmStartMLP(np.load(args.load_net)), [{"loaded": args.load_net}]
     else:
         net, record = train_warm_start(n_snakes=2048, rounds=2, skip=SKIP, target_warm=args.target_warm,
-                                       deploy=LEARNED if args.train_schedule == "deploy" else None)
+                                       deploy=learned if args.train_schedule == "deploy" else None)
     if args.save_net:
         np.save(args.save_net, net.params())
     t_train = time.perf_counter() - t_train
@@ -218,10 +223,11 @@ def run_gpu(args):
     sim.snapshot_save()
 
     modes = [("plain", dict(warm=0, beta=1.0)), ("previous", dict(warm=1, beta=0.5)),
-             ("learned", dict(warm=2, beta=SKIP, **LEARNED))]
+             ("learned", dict(warm=2, beta=SKIP, **learned))]
     if not args.no_learned_variants:
-        # the network on the bilateral rows only, and every second / fourth substep only
-        modes += [("learned_" + k, dict(warm=2, beta=SKIP, **v)) for k, v in LEARNED_VARIANTS.items()]
+        # the network on other row kinds and at other periods
+        modes += [("learned_" + k, dict(warm=2, beta=SKIP, **v)) for k, v in LEARNED_VARIANTS.items()
+                  if v != learned]
     results = {}
     clk_all = None
     layouts = {}
@@ -288,7 +294,7 @@ def run_gpu(args):
     # end to end, learned mode, through the public C-ABI with the state in pinned host
     # memory (is_device = 0: the library copies in and out): the same K env-steps from the
     # same start, state copied in and out every step
-    sim.set_config(warm=2, beta=SKIP, **LEARNED)
+    sim.set_config(warm=2, beta=SKIP, **learned)
     sim.snapshot_restore()
     start = sim.state()
     pin = lambda t: t.cpu().pin_memory()
@@ -310,7 +316,7 @@ def run_gpu(args):
     # per-layout kernel times of the learned step (direct launches with an event pair
     # around every solver kernel, on the stream it is launched on), for the roofline of
     # the dominant kernel
-    sim.set_config(warm=2, beta=SKIP, **LEARNED)
+    sim.set_config(warm=2, beta=SKIP, **learned)
     sim.snapshot_restore()
     sim.step(1)
     sim.kernel_times()
@@ -378,8 +384,9 @@ def run_gpu(args):
             "dtype": "f32",
             "data": "synthetic",
             "mode": "learned warm start (network trained on the plain solver's data, disjoint seeds; "
-                    "bilateral rows, every 2nd substep)",
-            "learned_config": dict(LEARNED, beta=SKIP, target_warm=args.target_warm,
+                    "%s rows, network every %d substep(s))" % (("all", "bilateral", "stretch")[learned["net_rows"]],
+                                                                learned["net_every"]),
+            "learned_config": dict(learned, beta=SKIP, target_warm=args.target_warm,
                                    train_schedule=args.train_schedule),
             "previous_value": modes_out["previous"]["value"],
             "learned_vs_previous": value / modes_out["previous"]["value"],
@@ -801,9 +808,13 @@ def main():
                          "1 beta x the previous multipliers")
     ap.add_argument("--no-learned-variants", action="store_true",
                     help="time only the headline learned configuration (not its variants)")
-    ap.add_argument("--train-schedule", default="all", choices=["all", "deploy"],
-                    help="row kinds and period of the network on the learned training "
-                         "trajectories: every row and substep, or the metric's learned configuration")
+    ap.add_argument("--net-rows", type=int, default=LEARNED["net_rows"], choices=[0, 1, 2],
+                    help="row kinds of the timed learned warm start: 0 all, 1 bilateral, 2 stretch")
+    ap.add_argument("--net-every", type=int, default=LEARNED["net_every"],
+                    help="the timed learned warm start runs the network every this many substeps")
+    ap.add_argument("--train-schedule", default="deploy", choices=["all", "deploy"],
+                    help="row kinds and period of the network on the learned training trajectories: "
+                         "every row and substep, or the timed configuration (--net-rows, --net-every)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default lane layouts instead of timing them per mode (sim_autotune)")
     ap.add_argument("--no-configs", action="store_true",

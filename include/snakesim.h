@@ -357,7 +357,9 @@ SimStatus sim_set_mlp(SimHandle* h, MlpHandle* m);
  * the features of every row.  sim_split_finish completes the current substep (warm start
  * per the configuration, iterations, velocities) and begins the next one, writing its
  * features; after the last substep the env-step counter advances.  Rows are
- * 6 * total_nodes (six slots per node). */
+ * 6 * total_nodes (six slots per node).  In the learned warm start only the row kinds
+ * the network predicts (net_rows) are written; the rows of the other kinds keep what an
+ * earlier write left there (zero in a new handle). */
 SimStatus sim_split_begin(SimHandle* h);
 SimStatus sim_split_finish(SimHandle* h);
 /* Device pointer of the feature buffer [rows][32] bf16 and the row count.  The rows of
@@ -373,9 +375,11 @@ SimStatus sim_feature_offsets(SimHandle* h, int32_t* first_row);
  * target that makes the warm start land on a reference solution lambda_star is
  *   y* = (lambda_star - beta lambda_prev) / (m g h^2)
  * with m the snake's node mass, g = 9.81 m/s^2 and h = dt / n_sub of the current
- * configuration.  For every existing row of the substep (the rows whose features carry
- * a row kind: stretch rows of nodes 0 .. N-2, yaw and pitch rows of nodes 1 .. N-2, and
- * with contact on the contact and two friction rows of every free node), snake by snake
+ * configuration.  For every existing row of the substep whose kind has its features
+ * written (the rows whose features carry a row kind: stretch rows of nodes 0 .. N-2,
+ * yaw and pitch rows of nodes 1 .. N-2, and with contact on the contact and two friction
+ * rows of every free node; in the learned warm start only the kinds of net_rows, as
+ * configured at this call), snake by snake
  * and node by node with the row kinds in order, the call copies the row's 32 bf16
  * features to feat_out and writes y* to target_out.
  * lam_star, lam_prev: device FP32 [nodes][6] in node order (the layout of

@@ -17,20 +17,29 @@ constexpr int layout_lanes(int id) { return 8 << (id / 4); }
 constexpr int layout_npl(int id) { return id % 4 + 1; }
 constexpr int kNumLayouts = 12;
 
+// Row kinds whose warm-start features are written: in the learned warm start the kinds
+// the network predicts (the first 6, 3 or 1 of stretch, yaw, pitch, contact, friction
+// x / y), otherwise all six.
+__host__ __device__ inline int feature_kinds(int warm, int net_rows) {
+  if (warm != SIM_WARM_LEARNED) return 6;
+  return net_rows == SIM_NET_ROWS_BILATERAL ? 3 : net_rows == SIM_NET_ROWS_STRETCH ? 1 : 6;
+}
 // Row slot k of node i (six per node: stretch to i + 1, yaw and pitch bend centred on
 // i, contact, friction x / y) of a snake of N nodes whose first nfix nodes are held:
-// whether the row exists, i.e. whether its warm-start features carry a row kind.
-__host__ __device__ inline bool feature_row_exists(int i, int k, int N, int nfix, int contact) {
+// whether the row exists and is of one of the first nk kinds, i.e. whether its
+// warm-start features carry a row kind.
+__host__ __device__ inline bool feature_row_exists(int i, int k, int N, int nfix, int contact, int nk) {
+  if (k >= nk) return false;
   if (k == 0) return i + 1 <= N - 1;
   if (k <= 2) return i >= 1 && i + 1 <= N - 1;
   return contact != 0 && i >= nfix;
 }
-// Existing rows of the node slots before node i (node by node, kinds in order).
-__host__ __device__ inline int feature_rows_before(int i, int N, int nfix, int contact) {
+// Such rows of the node slots before node i (node by node, kinds in order).
+__host__ __device__ inline int feature_rows_before(int i, int N, int nfix, int contact, int nk) {
   const int st = i < N - 1 ? i : N - 1;   // stretch rows of nodes 0 .. min(i, N - 1) - 1
   const int bd = st > 1 ? st - 1 : 0;     // bend pairs of nodes 1 .. min(i, N - 1) - 1
   const int ct = contact != 0 && i > nfix ? i - nfix : 0;
-  return st + 2 * bd + 3 * ct;
+  return st + (nk >= 3 ? 2 * bd : 0) + (nk >= 6 ? 3 * ct : 0);
 }
 
 struct SolverArgs {
@@ -73,6 +82,7 @@ struct SolverArgs {
   int pcr_iters;          // SIM_SOLVER_NEWTON_PCR: PCR iterations per Newton step
   int net_rows;           // SIM_WARM_LEARNED: SIM_NET_ROWS_*
   int net_every;          // SIM_WARM_LEARNED: the network's substeps are multiples of it (>= 1)
+  int feat_kinds;         // split mode: row kinds whose features are written (feature_kinds)
   int span;               // split mode: substeps the launch finishes (the first one with the
                           // network's start, the others from beta lambda_prev)
 };

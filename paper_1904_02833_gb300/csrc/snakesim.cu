@@ -204,15 +204,17 @@ __global__ void unpack_xyz_kernel(const float* __restrict__ in, float4* __restri
 }
 
 // Training rows of the learned warm start (sim_training_rows): one warp per snake, lanes
-// over its nodes.  Every existing row (feature_row_exists) of node i goes to output row
-// out_off[s] + feature_rows_before(i) + (existing kinds of node i before k): its features
+// over its nodes.  Every existing row of the nk written kinds (feature_row_exists) of
+// node i goes to output row out_off[s] + feature_rows_before(i) + (such kinds of node i
+// before k): its features
 // are copied and its target is (lam_star - beta lam_prev) / (m g h^2), the network's
 // output that would turn the warm start beta lam_prev + m g h^2 y into lam_star.
 __global__ void training_rows_kernel(const __nv_bfloat16* __restrict__ feat, const int* __restrict__ feat_off,
                                      const int* __restrict__ node_off, const SnakeParams* __restrict__ prm,
                                      const long long* __restrict__ out_off, const float* __restrict__ lam_star,
                                      const float* __restrict__ lam_prev, float beta, float h, int contact,
-                                     int n, __nv_bfloat16* __restrict__ feat_out, float* __restrict__ target_out) {
+                                     int nk, int n, __nv_bfloat16* __restrict__ feat_out,
+                                     float* __restrict__ target_out) {
   const int s = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
   if (s >= n) return;
@@ -220,10 +222,10 @@ __global__ void training_rows_kernel(const __nv_bfloat16* __restrict__ feat, con
   const int N = P.n_links * P.seg_per_link + 1;
   const float inv = 1.0f / (P.mass * 9.81f * h * h);
   for (int i = lane; i < N; i += 32) {
-    long long o = out_off[s] + feature_rows_before(i, N, P.n_fixed, contact);
+    long long o = out_off[s] + feature_rows_before(i, N, P.n_fixed, contact, nk);
     const long long g = (long long)node_off[s] + i;
     for (int k = 0; k < 6; ++k) {
-      if (!feature_row_exists(i, k, N, P.n_fixed, contact)) continue;
+      if (!feature_row_exists(i, k, N, P.n_fixed, contact, nk)) continue;
       const uint4* src = reinterpret_cast<const uint4*>(feat + ((long long)(feat_off[s] + i) * 6 + k) * 32);
       uint4* dst = reinterpret_cast<uint4*>(feat_out + o * 32);
 #pragma unroll
@@ -489,6 +491,7 @@ SolverArgs make_args(SimHandle* h, int n_steps) {
   A.pcr_iters = h->cfg.pcr_iters;
   A.net_rows = h->cfg.net_rows;
   A.net_every = std::max(1, h->cfg.net_every);
+  A.feat_kinds = feature_kinds(h->cfg.warm, h->cfg.net_rows);
   A.span = 1;
   return A;
 }
@@ -742,6 +745,7 @@ SimStatus sim_create(const SimConfig* cfg, int n_snakes, const SnakeParams* para
   CUC(cudaMemcpy(h->vel, vel.data(), h->n_nodes * sizeof(float4), cudaMemcpyHostToDevice));
   CUC(cudaMemset(h->press, 0, h->n_links * sizeof(float2)));
   CUC(cudaMemset(h->lam, 0, h->n_nodes * 6 * sizeof(float)));
+  CUC(cudaMemset(h->feat, 0, h->n_nodes * 6 * 32 * sizeof(__nv_bfloat16)));
   CUC(cudaMemcpy(h->prm, params, n_snakes * sizeof(SnakeParams), cudaMemcpyHostToDevice));
   CUC(cudaMemcpy(h->node_off_d, h->node_off.data(), (n_snakes + 1) * sizeof(int), cudaMemcpyHostToDevice));
   CUC(cudaMemcpy(h->link_off_d, h->link_off.data(), (n_snakes + 1) * sizeof(int), cudaMemcpyHostToDevice));
@@ -1093,11 +1097,12 @@ SimStatus sim_training_rows(SimHandle* h, const float* lam_star, const float* la
   if (!h || !n_rows) return fail(SIM_EINVAL, "null handle or row count");
   if (h->cur_sub < 0) return fail(SIM_EINVAL, "no substep in progress (sim_split_begin)");
   const int contact = h->cfg.contact;
+  const int nk = feature_kinds(h->cfg.warm, h->cfg.net_rows);
   h->train_off_h.assign(h->n + 1, 0);
   for (int s = 0; s < h->n; ++s) {
     const SnakeParams& p = h->hprm[s];
     const int N = p.n_links * p.seg_per_link + 1;
-    h->train_off_h[s + 1] = h->train_off_h[s] + feature_rows_before(N, N, p.n_fixed, contact);
+    h->train_off_h[s + 1] = h->train_off_h[s] + feature_rows_before(N, N, p.n_fixed, contact, nk);
   }
   const long long total = h->train_off_h[h->n];
   *n_rows = total;
@@ -1113,7 +1118,7 @@ SimStatus sim_training_rows(SimHandle* h, const float* lam_star, const float* la
   const int threads = 256, blocks = (int)((32LL * h->n + threads - 1) / threads);
   training_rows_kernel<<<blocks, threads, 0, h->stream>>>(
       h->feat, h->feat_off_d, h->node_off_d, h->prm, h->train_off, lam_star, lam_prev, beta,
-      (float)(h->cfg.dt / h->cfg.n_sub), contact, h->n, (__nv_bfloat16*)feat_out, target_out);
+      (float)(h->cfg.dt / h->cfg.n_sub), contact, nk, h->n, (__nv_bfloat16*)feat_out, target_out);
   CU(cudaGetLastError());
   h->launches += 1;
   return SIM_OK;

@@ -393,7 +393,8 @@ __device__ __forceinline__ float row_pass(const SnakeK& S, const SolverArgs& A, 
 // the row's first node above its contact height / L0 (1); positions of the row's second
 // and third node relative to the first, in the frame, / L0 (6); velocities of the up to
 // three nodes in the frame, x h / L0 (9); rest angle of a yaw row (1); the row's
-// multiplier from the previous substep / (m g h^2) (1).  Rows that do not exist are zero.
+// multiplier from the previous substep / (m g h^2) (1).  Rows that do not exist are zero;
+// only the first A.feat_kinds kinds are written (the kinds the network predicts).
 template <int NPL, int G>
 __device__ __forceinline__ void write_features(const SnakeK& S, const SolverArgs& A, int q, bool valid,
                                                const float (&xs)[NPL][3], const float (&dx)[NPL][3],
@@ -436,10 +437,11 @@ __device__ __forceinline__ void write_features(const SnakeK& S, const SolverArgs
     const bool has_next = i + 1 <= S.N - 1;
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
+      if (k >= A.feat_kinds) break;  // kinds the network does not predict are not written
       float f[32];
 #pragma unroll
       for (int c = 0; c < 32; ++c) f[c] = 0.f;
-      if (feature_row_exists(i, k, S.N, S.nfix, A.contact)) {
+      if (feature_row_exists(i, k, S.N, S.nfix, A.contact, 6)) {
         f[k] = 1.f;
         int na, nb = -1, nc = -1;  // local node indices 0..2 (i-1, i, i+1)
         float tx, ty;

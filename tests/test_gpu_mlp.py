@@ -235,6 +235,61 @@ def test_training_rows_match_oracle(contact):
     assert np.array_equal(g.features().float().cpu().numpy(), fnode)
 
 
+@pytest.mark.parametrize("net_rows,kinds", [(1, 3), (2, 1)])
+def test_learned_mode_writes_the_predicted_kinds_only(net_rows, kinds):
+    """In the learned warm start the feature writer fills only the row kinds the network
+    predicts (bilateral: stretch, yaw, pitch; stretch alone): those rows equal the
+    oracle's features, the other kinds' rows keep what was there (zero in a new handle),
+    and sim_training_rows emits the predicted kinds' existing rows only, in the oracle's
+    order with the oracle's targets."""
+    from paper_1904_02833_gb300.mlp import WarmStartMLP
+    from paper_1904_02833_gb300.sim import SnakeSim
+    w = W.batched(n=21, seed=36, links=(1, 8))
+    w["n_fixed"][:3] = [0, 1, 2]
+    beta = 0.5
+    s = W.solver_settings(iters=10)
+    g, o = SnakeSim(w, s), oracle.OracleSim(w, s)
+    g.step(3)
+    o.step(3)
+    net = WarmStartMLP(M.init_params(11) * 0.5)
+    g.set_mlp(net)
+    learned = dict(s, warm=2, beta=beta, net_rows=net_rows)
+    g.set_config(**learned)
+    g.split_begin()
+    fg = g.features().float().cpu().numpy()
+    fo = o.features()
+    kind = np.arange(len(fg)) % 6
+    assert not fg[kind >= kinds].any()
+    sel = kind < kinds
+    err = np.abs(fg[sel, :24] - fo[sel, :24])
+    assert (err[:, :23] <= 1e-2 * np.abs(fo[sel, :23]) + 2e-3).all(), err[:, :23].max()
+    assert (err[:, 23] <= 5e-3 * np.abs(fo[sel, 23]).max() + 1e-2 * np.abs(fo[sel, 23])).all()
+    # training rows of the substep in progress, targets from a tight solve on a snapshot
+    lam_prev = g.lam().clone()
+    g.snapshot_save()
+    g.set_config(tol=1e-6, iters=20000, warm=0)
+    g.split_finish()
+    lam_star = g.lam().clone()
+    g.snapshot_restore()
+    g.set_config(**learned)
+    F, T = g.training_rows(lam_star, lam_prev, beta)
+    F, T = F.float().cpu().numpy(), T.cpu().numpy()
+    fnode = g.features().float().cpu().numpy()
+    assert np.array_equal(fnode, fg)
+    nn = W.n_nodes(w).astype(np.int64)
+    expect = (nn - 1) + (2 * (nn - 2) if kinds >= 3 else 0)
+    h = s["dt"] / s["n_sub"]
+    Fo, To = M.training_rows(g.node_off, w["mass"], fnode, lam_star.cpu().numpy().astype(np.float64),
+                             lam_prev.cpu().numpy().astype(np.float64), beta, h)
+    assert len(T) == len(To) == int(expect.sum())
+    assert np.array_equal(F, Fo)
+    assert np.all(np.argmax(F[:, :6], 1) < kinds)
+    scale = (np.abs(lam_star.cpu().numpy()).max() + np.abs(lam_prev.cpu().numpy()).max()) / (w["mass"].min() * 9.81 * h * h)
+    assert np.abs(T - To).max() <= 1e-6 * scale
+    g.close()
+    net.close()
+
+
 def test_snapshot_branch_inside_a_split_step_is_invisible():
     """Saving inside a split env-step, finishing the substep with another configuration,
     restoring and finishing it in the learned mode gives, bit for bit, what a run that

@@ -469,8 +469,8 @@ class _Rows:
 def test_benchmark_configuration_sampled_parity():
     """The benchmark's launch configuration: the 16384-snake evaluation batch, lane layouts
     autotuned per mode, Jacobi to residual 1e-4; plain, previous-multiplier and learned
-    (the benchmark's own learned settings: the network on the bilateral rows at every
-    second substep, spans of two substeps per launch) env-steps from one state; 12 sampled snakes recomputed by the oracle alone
+    (the benchmark's own learned settings, `bench.LEARNED`: the network on the bilateral
+    rows every few substeps, a span of substeps per launch) env-steps from one state; 12 sampled snakes recomputed by the oracle alone
     (snakes are independent).  To a tolerance FP32 and FP64 may stop a substep a few
     updates apart, hence the velocity floor and the count bound."""
     from oracle import mlp_oracle as M
