@@ -183,6 +183,9 @@ def run_gpu(args):
     if args.net_every < 1:
         raise SystemExit("--net-every must be >= 1")
     learned = dict(net_rows=args.net_rows, net_every=args.net_every)
+    skip = float(args.skip)
+    if not 0.0 <= skip <= 1.0:
+        raise SystemExit("--skip must lie in [0, 1]")
     if world > 1:
         dist.init_process_group("nccl")
     from paper_1904_02833_gb300.mlp import train_warm_start
@@ -199,7 +202,8 @@ def run_gpu(args):
         from paper_1904_02833_gb300.mlp import WarmStartMLP
         net, record = WarmStartMLP(np.load(args.load_net)), [{"loaded": args.load_net}]
     else:
-        net, record = train_warm_start(n_snakes=2048, rounds=2, skip=SKIP, target_warm=args.target_warm,
+        net, record = train_warm_start(n_snakes=args.train_snakes, rounds=args.train_rounds, skip=skip,
+                                       target_warm=args.target_warm,
                                        deploy=learned if args.train_schedule == "deploy" else None)
     if args.save_net:
         np.save(args.save_net, net.params())
@@ -223,10 +227,10 @@ def run_gpu(args):
     sim.snapshot_save()
 
     modes = [("plain", dict(warm=0, beta=1.0)), ("previous", dict(warm=1, beta=0.5)),
-             ("learned", dict(warm=2, beta=SKIP, **learned))]
+             ("learned", dict(warm=2, beta=skip, **learned))]
     if not args.no_learned_variants:
         # the network on other row kinds and at other periods
-        modes += [("learned_" + k, dict(warm=2, beta=SKIP, **v)) for k, v in LEARNED_VARIANTS.items()
+        modes += [("learned_" + k, dict(warm=2, beta=skip, **v)) for k, v in LEARNED_VARIANTS.items()
                   if v != learned]
     results = {}
     clk_all = None
@@ -294,7 +298,7 @@ def run_gpu(args):
     # end to end, learned mode, through the public C-ABI with the state in pinned host
     # memory (is_device = 0: the library copies in and out): the same K env-steps from the
     # same start, state copied in and out every step
-    sim.set_config(warm=2, beta=SKIP, **learned)
+    sim.set_config(warm=2, beta=skip, **learned)
     sim.snapshot_restore()
     start = sim.state()
     pin = lambda t: t.cpu().pin_memory()
@@ -316,7 +320,7 @@ def run_gpu(args):
     # per-layout kernel times of the learned step (direct launches with an event pair
     # around every solver kernel, on the stream it is launched on), for the roofline of
     # the dominant kernel
-    sim.set_config(warm=2, beta=SKIP, **learned)
+    sim.set_config(warm=2, beta=skip, **learned)
     sim.snapshot_restore()
     sim.step(1)
     sim.kernel_times()
@@ -386,7 +390,7 @@ def run_gpu(args):
             "mode": "learned warm start (network trained on the plain solver's data, disjoint seeds; "
                     "%s rows, network every %d substep(s))" % (("all", "bilateral", "stretch")[learned["net_rows"]],
                                                                 learned["net_every"]),
-            "learned_config": dict(learned, beta=SKIP, target_warm=args.target_warm,
+            "learned_config": dict(learned, beta=skip, target_warm=args.target_warm,
                                    train_schedule=args.train_schedule),
             "previous_value": modes_out["previous"]["value"],
             "learned_vs_previous": value / modes_out["previous"]["value"],
@@ -812,6 +816,11 @@ def main():
                     help="row kinds of the timed learned warm start: 0 all, 1 bilateral, 2 stretch")
     ap.add_argument("--net-every", type=int, default=LEARNED["net_every"],
                     help="the timed learned warm start runs the network every this many substeps")
+    ap.add_argument("--skip", type=float, default=SKIP,
+                    help="beta of the learned warm start (lambda0 = beta lambda_prev + m g h^2 y)")
+    ap.add_argument("--train-rounds", type=int, default=2,
+                    help="on-policy training rounds after the cold-start round")
+    ap.add_argument("--train-snakes", type=int, default=2048, help="snakes per training batch")
     ap.add_argument("--train-schedule", default="deploy", choices=["all", "deploy"],
                     help="row kinds and period of the network on the learned training trajectories: "
                          "every row and substep, or the timed configuration (--net-rows, --net-every)")
