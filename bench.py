@@ -226,7 +226,7 @@ def run_gpu(args):
     barrier()
     sim.snapshot_save()
 
-    modes = [("plain", dict(warm=0, beta=1.0)), ("previous", dict(warm=1, beta=0.5)),
+    modes = [("plain", dict(warm=0, beta=1.0)), ("previous", dict(warm=1, beta=args.prev_beta)),
              ("learned", dict(warm=2, beta=skip, **learned))]
     if not args.no_learned_variants:
         # the network on other row kinds and at other periods
@@ -818,6 +818,8 @@ def main():
                     help="the timed learned warm start runs the network every this many substeps")
     ap.add_argument("--skip", type=float, default=SKIP,
                     help="beta of the learned warm start (lambda0 = beta lambda_prev + m g h^2 y)")
+    ap.add_argument("--prev-beta", type=float, default=0.5,
+                    help="beta of the previous-multiplier warm start (lambda0 = beta lambda_prev)")
     ap.add_argument("--train-rounds", type=int, default=2,
                     help="on-policy training rounds after the cold-start round")
     ap.add_argument("--train-snakes", type=int, default=2048, help="snakes per training batch")

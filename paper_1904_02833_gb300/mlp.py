@@ -98,10 +98,12 @@ def collect(sim, n_steps: int, substeps=None, every: int = 1, target_tol: float 
     the previous multipliers the deployed solver produces.  At each logged substep the
     substep is also solved from the same start to `target_tol` on a snapshot (from zero
     multipliers, target_warm = 0, or from beta times the previous ones, target_warm = 1);
-    sim_training_rows then writes every existing row's features and its target
-    (the multiplier reached there minus beta times the previous multiplier, over
-    m g h^2: the network predicts the correction to the beta-weighted previous
-    multiplier).  Returns bf16 features [n, 32] and float targets [n], on the device."""
+    sim_training_rows then writes the features and target (the multiplier reached there
+    minus beta times the previous multiplier, over m g h^2: the network predicts the
+    correction to the beta-weighted previous multiplier) of every existing row whose
+    features the simulator writes (all kinds; in the learned warm start, the kinds the
+    network predicts).  Returns bf16 features [n, 32] and float targets [n], on the
+    device."""
     w = dict(sim.settings)
     n_sub = w["n_sub"]
     beta = float(w.get("beta", 1.0)) if skip is None else float(skip)
