@@ -39,6 +39,8 @@ SKIP = 0.5  # learned warm start: lambda0 = SKIP lambda_prev + m g h^2 network(f
 # (every second substep ran as fast, every third ends fewer launches on their slowest
 # snake); the other variants, with the same network, are reported under `modes`
 LEARNED = dict(net_rows=1, net_every=3)
+LEARNED_BETA = SKIP  # weight of lambda_prev at the learned mode's substeps without the network
+PREV_BETA = 0.5      # the previous-multiplier warm start's weight of lambda_prev
 TARGET_WARM = 1  # training targets: solves started from SKIP x the previous multipliers
 LEARNED_VARIANTS = {"all_every1": dict(net_rows=0, net_every=1), "bilateral_every1": dict(net_rows=1, net_every=1),
                     "bilateral_every2": dict(net_rows=1, net_every=2), "bilateral_every3": dict(net_rows=1, net_every=3),
@@ -182,10 +184,13 @@ def run_gpu(args):
     torch.cuda.set_device(local)
     if args.net_every < 1:
         raise SystemExit("--net-every must be >= 1")
-    learned = dict(net_rows=args.net_rows, net_every=args.net_every)
     skip = float(args.skip)
-    if not 0.0 <= skip <= 1.0:
-        raise SystemExit("--skip must lie in [0, 1]")
+    lbeta = float(args.learned_beta)
+    if not (0.0 <= skip <= 1.0 and 0.0 <= lbeta <= 1.0):
+        raise SystemExit("--skip and --learned-beta must lie in [0, 1]")
+    # the timed learned warm start: the network's prediction on skip x lambda_prev at its
+    # substeps, lbeta x lambda_prev elsewhere
+    learned = dict(net_rows=args.net_rows, net_every=args.net_every, beta=lbeta, beta_net=skip)
     if world > 1:
         dist.init_process_group("nccl")
     from paper_1904_02833_gb300.mlp import train_warm_start
@@ -204,7 +209,9 @@ def run_gpu(args):
     else:
         net, record = train_warm_start(n_snakes=args.train_snakes, rounds=args.train_rounds, skip=skip,
                                        target_warm=args.target_warm,
-                                       deploy=learned if args.train_schedule == "deploy" else None)
+                                       deploy=(dict(net_rows=learned["net_rows"], net_every=learned["net_every"],
+                                                    beta=learned["beta"])
+                                               if args.train_schedule == "deploy" else None))
     if args.save_net:
         np.save(args.save_net, net.params())
     t_train = time.perf_counter() - t_train
@@ -227,11 +234,11 @@ def run_gpu(args):
     sim.snapshot_save()
 
     modes = [("plain", dict(warm=0, beta=1.0)), ("previous", dict(warm=1, beta=args.prev_beta)),
-             ("learned", dict(warm=2, beta=skip, **learned))]
+             ("learned", dict(warm=2, **learned))]
     if not args.no_learned_variants:
         # the network on other row kinds and at other periods
-        modes += [("learned_" + k, dict(warm=2, beta=skip, **v)) for k, v in LEARNED_VARIANTS.items()
-                  if v != learned]
+        modes += [("learned_" + k, dict(warm=2, beta=skip, beta_net=skip, **v))
+                  for k, v in LEARNED_VARIANTS.items() if dict(v, beta=skip, beta_net=skip) != learned]
     results = {}
     clk_all = None
     layouts = {}
@@ -298,7 +305,7 @@ def run_gpu(args):
     # end to end, learned mode, through the public C-ABI with the state in pinned host
     # memory (is_device = 0: the library copies in and out): the same K env-steps from the
     # same start, state copied in and out every step
-    sim.set_config(warm=2, beta=skip, **learned)
+    sim.set_config(warm=2, **learned)
     sim.snapshot_restore()
     start = sim.state()
     pin = lambda t: t.cpu().pin_memory()
@@ -320,7 +327,7 @@ def run_gpu(args):
     # per-layout kernel times of the learned step (direct launches with an event pair
     # around every solver kernel, on the stream it is launched on), for the roofline of
     # the dominant kernel
-    sim.set_config(warm=2, beta=skip, **learned)
+    sim.set_config(warm=2, **learned)
     sim.snapshot_restore()
     sim.step(1)
     sim.kernel_times()
@@ -390,7 +397,7 @@ def run_gpu(args):
             "mode": "learned warm start (network trained on the plain solver's data, disjoint seeds; "
                     "%s rows, network every %d substep(s))" % (("all", "bilateral", "stretch")[learned["net_rows"]],
                                                                 learned["net_every"]),
-            "learned_config": dict(learned, beta=skip, target_warm=args.target_warm,
+            "learned_config": dict(learned, target_warm=args.target_warm,
                                    train_schedule=args.train_schedule),
             "previous_value": modes_out["previous"]["value"],
             "learned_vs_previous": value / modes_out["previous"]["value"],
@@ -817,8 +824,11 @@ def main():
     ap.add_argument("--net-every", type=int, default=LEARNED["net_every"],
                     help="the timed learned warm start runs the network every this many substeps")
     ap.add_argument("--skip", type=float, default=SKIP,
-                    help="beta of the learned warm start (lambda0 = beta lambda_prev + m g h^2 y)")
-    ap.add_argument("--prev-beta", type=float, default=0.5,
+                    help="weight of lambda_prev under the network's prediction "
+                         "(lambda0 = skip lambda_prev + m g h^2 y)")
+    ap.add_argument("--learned-beta", type=float, default=LEARNED_BETA,
+                    help="weight of lambda_prev at the learned mode's substeps without the network")
+    ap.add_argument("--prev-beta", type=float, default=PREV_BETA,
                     help="beta of the previous-multiplier warm start (lambda0 = beta lambda_prev)")
     ap.add_argument("--train-rounds", type=int, default=2,
                     help="on-policy training rounds after the cold-start round")

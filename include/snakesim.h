@@ -74,7 +74,9 @@ typedef struct {
   int32_t warm;       /* SIM_WARM_*                                                      */
   float beta;         /* weight of the previous substep's multipliers in a warm start:   *
                        * PREVIOUS starts from beta lambda_prev, LEARNED from              *
-                       * beta lambda_prev + m g h^2 y (y: the network's output)          */
+                       * beta_net lambda_prev + m g h^2 y (y: the network's output) on    *
+                       * the rows the network predicts and from beta lambda_prev on the   *
+                       * others and at the substeps between network substeps             */
   int32_t latency;    /* chamber model, SIM_LATENCY_*                                    */
   /* SIM_LATENCY_LAW only (Sec. V-A, Eq. 11-12; pressures in units of the maximum):      *
    * every law_dt seconds (rounded to whole substeps, at least one) each chamber moves    *
@@ -94,6 +96,8 @@ typedef struct {
   int32_t net_every;  /* the network runs at substeps s with s % net_every == 0 (0 is     *
                        * read as 1); the substeps in between start from beta lambda_prev  *
                        * and run in the same launch as the network substep before them   */
+  float beta_net;     /* weight of lambda_prev under the network's prediction, <= 1; a    *
+                       * negative value means beta                                        */
 } SimConfig;
 
 /* Row kinds the network predicts in the learned warm start: all six (stretch, yaw, pitch,

@@ -83,7 +83,7 @@ def pack_cfg(s: dict) -> np.ndarray:
                      s.get("latency", 0), s.get("k_inflate", 0.23), s.get("k_deflate", 0.23),
                      s.get("t_p", 0.085), s.get("p_source", 1.0), s.get("law_dt", 0.0083),
                      s.get("solver", 0), s.get("pcr_iters", 20), s.get("net_rows", 0),
-                     s.get("net_every", 1)], np.float64)
+                     s.get("net_every", 1), s.get("beta_net", -1.0)], np.float64)
 
 
 class OracleSim:

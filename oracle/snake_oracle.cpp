@@ -106,7 +106,8 @@ enum { P_L0, P_MASS, P_ALPHA_S, P_ALPHA_B, P_GAIN, P_TAU_INF, P_TAU_DEF, P_MU, P
        P_RADIUS, P_AMP, P_FREQ, P_LAG, P_OFFSET, P_SCALE, P_ALT, P_X0, P_Y0, P_Z0, P_YAW0,
        P_MU_SIDE, NPRM };
 enum { C_DT, C_NSUB, C_ITERS, C_TOL, C_OMEGA, C_GX, C_GY, C_GZ, C_CONTACT, C_WARM, C_BETA,
-       C_LATENCY, C_KI, C_KD, C_TP, C_PS, C_LAW_DT, C_SOLVER, C_PCR_ITERS, C_NET_ROWS, C_NET_EVERY, NCFG };
+       C_LATENCY, C_KI, C_KD, C_TP, C_PS, C_LAW_DT, C_SOLVER, C_PCR_ITERS, C_NET_ROWS, C_NET_EVERY,
+       C_BETA_NET, NCFG };
 // Row kinds; a node i owns one multiplier slot per kind: stretch (i, i+1), yaw and
 // pitch bend centred on i, contact of i, friction of i along world x and y.
 enum { R_STRETCH, R_YAW, R_PITCH, R_CONTACT, R_FX, R_FY, NK };
@@ -162,6 +163,7 @@ void project_ellipse(T& px, T& py, double tx, double ty, double mu_t, double mu_
 
 struct Cfg {
   double dt, h, tol, omega, g[3], beta;
+  double beta_net;               // learned warm start: weight of lambda_prev under the prediction
   int n_sub, iters, contact, warm;
   int latency, law_every;        // chamber model (0 exponential, 1 Sec. V-A law), its period
   double k_i, k_d, t_p, p_s;     // Sec. V-A law: gains, deflation threshold, source pressure
@@ -178,6 +180,7 @@ Cfg load_cfg(const double* c) {
   C.law_every = std::max(1, (int)std::llround(c[C_LAW_DT] / C.h));
   C.solver = (int)c[C_SOLVER]; C.pcr_iters = (int)c[C_PCR_ITERS];
   C.net_rows = (int)c[C_NET_ROWS]; C.net_every = std::max(1, (int)c[C_NET_EVERY]);
+  C.beta_net = c[C_BETA_NET] < 0.0 ? C.beta : c[C_BETA_NET];
   return C;
 }
 
@@ -659,23 +662,28 @@ double snake_step(const Snake<T>& S, const Cfg& C, long long step_index, V3<T>* 
       }
     }
     if (feat0) { row_features(S, C, X, v, lam, theta, feat0); return 0.0; }
-    // multipliers: cold (0), beta x the previous substep's values, plus the network's
-    // prediction in the learned mode (at the substeps s with s % net_every == 0, for every
-    // row kind or the bilateral kinds only).  A non-zero start also moves the nodes by
+    // multipliers: cold (0), beta x the previous substep's values, or in the learned mode
+    // at the substeps s with s % net_every == 0, on the row kinds the network predicts
+    // (every kind, the bilateral kinds or the stretch rows), beta_net x the previous value
+    // plus the network's prediction.  A non-zero start also moves the nodes by
     // M^-1 J^T lambda0 (gradients at the predicted positions), so that
     // M (x - x~) = J^T lambda holds from the first iterate on.
     if (C.warm == 0) for (auto& l : lam) l = T(0.0);
     else {
       std::vector<double> y(lam.size(), 0.0);
+      std::vector<char> pred(lam.size(), 0);
       if (C.warm == 2 && mlp && s % C.net_every == 0) {
         std::vector<double> F((size_t)N * NK * kFeat);
         row_features(S, C, X, v, lam, theta, F.data());
         for (size_t j = 0; j < lam.size(); ++j)
-          if (C.net_rows == 0 || (int)(j % NK) <= (C.net_rows == 1 ? R_PITCH : R_STRETCH))
+          if (C.net_rows == 0 || (int)(j % NK) <= (C.net_rows == 1 ? R_PITCH : R_STRETCH)) {
+            pred[j] = 1;
             y[j] = mlp_forward(mlp, &F[j * kFeat]);
+          }
       }
       const double sc = val(S.mass) * 9.81 * h * h;
-      for (size_t j = 0; j < lam.size(); ++j) lam[j] = C.beta * lam[j] + T(y[j] * sc);
+      for (size_t j = 0; j < lam.size(); ++j)
+        lam[j] = (pred[j] ? C.beta_net : C.beta) * lam[j] + T(y[j] * sc);
     }
     if (C.warm != 0) {
       eval_rows(S, C, X, XS, theta, R);

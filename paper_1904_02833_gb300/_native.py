@@ -26,7 +26,7 @@ class SimConfig(ctypes.Structure):
                 ("k_deflate", ctypes.c_float), ("t_p", ctypes.c_float),
                 ("p_source", ctypes.c_float), ("law_dt", ctypes.c_float),
                 ("solver", ctypes.c_int32), ("pcr_iters", ctypes.c_int32),
-                ("net_rows", ctypes.c_int32), ("net_every", ctypes.c_int32)]
+                ("net_rows", ctypes.c_int32), ("net_every", ctypes.c_int32), ("beta_net", ctypes.c_float)]
 
 
 SNAKE_FLOAT_FIELDS = ("L0", "mass", "alpha_s", "alpha_b", "gain", "tau_inf", "tau_def", "mu",
@@ -41,7 +41,7 @@ class SnakeParams(ctypes.Structure):
 
 
 assert ctypes.sizeof(SnakeParams) == 96
-assert ctypes.sizeof(SimConfig) == 88
+assert ctypes.sizeof(SimConfig) == 96
 
 
 # tetrahedral soft link (include/femlink.h)

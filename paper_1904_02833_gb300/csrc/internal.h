@@ -83,6 +83,7 @@ struct SolverArgs {
   int net_rows;           // SIM_WARM_LEARNED: SIM_NET_ROWS_*
   int net_every;          // SIM_WARM_LEARNED: the network's substeps are multiples of it (>= 1)
   int feat_kinds;         // split mode: row kinds whose features are written (feature_kinds)
+  float beta_net;         // SIM_WARM_LEARNED: weight of lambda_prev under the prediction
   int span;               // split mode: substeps the launch finishes (the first one with the
                           // network's start, the others from beta lambda_prev)
 };

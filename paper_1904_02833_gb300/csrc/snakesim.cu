@@ -325,8 +325,10 @@ SimStatus validate_cfg(const SimConfig* c) {
     return fail(SIM_EINVAL, "invalid config: solver must be SIM_SOLVER_JACOBI or SIM_SOLVER_NEWTON_PCR");
   if (c->solver == SIM_SOLVER_NEWTON_PCR && (c->contact != 0 || c->pcr_iters < 1))
     return fail(SIM_EINVAL, "the Newton + PCR solver needs contact = 0 and pcr_iters >= 1");
-  if (c->net_rows < SIM_NET_ROWS_ALL || c->net_rows > SIM_NET_ROWS_STRETCH || c->net_every < 0)
-    return fail(SIM_EINVAL, "invalid config: net_rows must be one of SIM_NET_ROWS_*, net_every >= 0");
+  if (c->net_rows < SIM_NET_ROWS_ALL || c->net_rows > SIM_NET_ROWS_STRETCH || c->net_every < 0 ||
+      !(c->beta_net <= 1.f))
+    return fail(SIM_EINVAL, "invalid config: net_rows must be one of SIM_NET_ROWS_*, net_every >= 0, "
+                            "beta_net <= 1");
   if (c->latency != SIM_LATENCY_EXP && c->latency != SIM_LATENCY_LAW)
     return fail(SIM_EINVAL, "invalid config: latency must be SIM_LATENCY_EXP or SIM_LATENCY_LAW");
   if (c->latency == SIM_LATENCY_LAW &&
@@ -492,6 +494,7 @@ SolverArgs make_args(SimHandle* h, int n_steps) {
   A.net_rows = h->cfg.net_rows;
   A.net_every = std::max(1, h->cfg.net_every);
   A.feat_kinds = feature_kinds(h->cfg.warm, h->cfg.net_rows);
+  A.beta_net = h->cfg.beta_net < 0.f ? h->cfg.beta : h->cfg.beta_net;
   A.span = 1;
   return A;
 }

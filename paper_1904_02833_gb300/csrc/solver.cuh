@@ -794,17 +794,18 @@ __device__ void run_group(const SolverArgs& A, int snake, bool valid, float* sme
 #pragma unroll
         for (int k = 0; k < 6; ++k) lam[j][k] = 0.f;
     } else {
-      // warm start: beta lambda_prev (+ m g h^2 y of the network)
+      // warm start: beta lambda_prev, or beta_net lambda_prev + m g h^2 y on the rows the
+      // network predicts at this substep
       const float sc = S.mass * 9.81f * h * h;
 #pragma unroll
       for (int j = 0; j < NPL; ++j) {
         const int i = q * NPL + j;
 #pragma unroll
         for (int k = 0; k < 6; ++k) {
-          float l = A.beta * lam[j][k];
-          if (A.warm == 2 && net && A.lam0 && valid && i < S.N &&
-              (A.net_rows == SIM_NET_ROWS_ALL || k < (A.net_rows == SIM_NET_ROWS_BILATERAL ? 3 : 1)))
-            l += A.lam0[(size_t)(S.fb + i) * 6 + k] * sc;
+          const bool pk = A.warm == 2 && net && A.lam0 && valid && i < S.N &&
+                          (A.net_rows == SIM_NET_ROWS_ALL || k < (A.net_rows == SIM_NET_ROWS_BILATERAL ? 3 : 1));
+          float l = (pk ? A.beta_net : A.beta) * lam[j][k];
+          if (pk) l += A.lam0[(size_t)(S.fb + i) * 6 + k] * sc;
           lam[j][k] = l;
         }
       }

@@ -164,8 +164,9 @@ def train_warm_start(n_snakes: int = 1024, seeds=None, rounds: int = 2, settle: 
     multipliers the plain solver reaches at `tol` from the same start (cold, or from
     `skip` times the previous multipliers with target_warm = 1), minus `skip` times the
     previous multipliers (the learned warm start adds the network's output to the
-    previous multipliers weighted by beta = skip).  `deploy` (net_rows, net_every) sets
-    the row kinds and period the learned trajectories use the network on, and the
+    previous multipliers weighted by beta = skip).  `deploy` (net_rows, net_every and
+    beta, the weight of the previous multipliers at the substeps without the network)
+    sets the row kinds and period the learned trajectories use the network on, and the
     logged substeps are then network substeps, so that the previous multipliers in the
     data come from the schedule the network will be deployed with.  All simulation and
     all training run in the library's kernels.  Returns the network and a record of the
@@ -185,7 +186,9 @@ def train_warm_start(n_snakes: int = 1024, seeds=None, rounds: int = 2, settle: 
         sim.step(settle)
         if learned:
             sim.set_mlp(net)
-            sim.set_config(warm=2, beta=skip, **deploy)
+            cfg = dict(warm=2, beta=skip)
+            cfg.update(deploy)
+            sim.set_config(beta_net=skip, **cfg)
             sim.step(2)
         logged = (0, 7, 14)
         if learned:  # the network substeps nearest to those

@@ -61,6 +61,7 @@ def make_config(s: dict) -> N.SimConfig:
     c.pcr_iters = int(s.get("pcr_iters", 20))
     c.net_rows = int(s.get("net_rows", 0))
     c.net_every = int(s.get("net_every", 1))
+    c.beta_net = float(s.get("beta_net", -1.0))
     return c
 
 

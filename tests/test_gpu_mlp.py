@@ -143,11 +143,13 @@ def test_split_stepping_matches_fused_stepping():
         assert np.abs(sa["vel"] - sb["vel"]).max() <= tol_x / h
 
 
-@pytest.mark.parametrize("net_rows,net_every", [(0, 1), (1, 1), (0, 4), (1, 7), (0, 20), (2, 1), (2, 3)])
-def test_learned_mode_matches_oracle(net_rows, net_every):
+@pytest.mark.parametrize("net_rows,net_every,beta", [(0, 1, 0.5), (1, 1, 0.5), (0, 4, 0.5), (1, 7, 0.5),
+                                                     (0, 20, 0.5), (2, 1, 0.5), (2, 3, 0.5), (1, 3, 0.75)])
+def test_learned_mode_matches_oracle(net_rows, net_every, beta):
     """Same network parameters on both sides; fixed iteration count; the network on all
     row kinds or the bilateral ones, at every substep or every net_every-th (the launches
-    then finish several substeps each)."""
+    then finish several substeps each), its prediction on 0.5 lambda_prev and the other
+    rows and substeps from beta lambda_prev."""
     from paper_1904_02833_gb300.sim import SnakeSim
     w = W.batched(n=16, seed=33, links=(1, 8))
     p = M.init_params(8) * 0.5
@@ -157,8 +159,8 @@ def test_learned_mode_matches_oracle(net_rows, net_every):
     o.step(2)
     net = mlp(p)
     g.set_mlp(net)
-    g.set_config(warm=2, net_rows=net_rows, net_every=net_every)
-    o.set_cfg(warm=2, net_rows=net_rows, net_every=net_every)
+    g.set_config(warm=2, net_rows=net_rows, net_every=net_every, beta=beta, beta_net=0.5)
+    o.set_cfg(warm=2, net_rows=net_rows, net_every=net_every, beta=beta, beta_net=0.5)
     g.step(1)
     o.step(1, mlp=p)
     # the parity bounds of tests/test_gpu_parity.py, with the floor of a solve started by

@@ -488,7 +488,8 @@ def test_benchmark_configuration_sampled_parity():
     p = M.init_params(11) * 0.5
     net = WarmStartMLP(p)
     g.set_mlp(net)
-    for cfg in (dict(warm=0), dict(warm=1, beta=0.5), dict(warm=2, beta=bench.SKIP, **bench.LEARNED)):
+    for cfg in (dict(warm=0), dict(warm=1, beta=bench.PREV_BETA),
+                dict(warm=2, beta=bench.LEARNED_BETA, beta_net=bench.SKIP, **bench.LEARNED)):
         g.set_config(**cfg)
         o.set_cfg(**cfg)
         g.autotune(1)

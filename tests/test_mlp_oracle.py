@@ -125,29 +125,36 @@ def test_training_target_inverts_the_learned_warm_start(beta):
     assert np.array_equal(F[:, :6].sum(1), np.ones(len(F)))
 
 
-@pytest.mark.parametrize("net_rows,net_every", [(0, 1), (0, 2), (1, 2), (1, 1), (2, 1), (2, 3)])
-def test_learned_warm_start_schedule_closed_form(net_rows, net_every):
+@pytest.mark.parametrize("net_rows,net_every,beta_net",
+                         [(0, 1, None), (0, 2, None), (1, 2, None), (1, 1, None), (2, 1, None), (2, 3, None),
+                          (1, 3, 0.25), (0, 2, 0.75), (2, 1, 0.0)])
+def test_learned_warm_start_schedule_closed_form(net_rows, net_every, beta_net):
     """Which substeps and row kinds take the network's prediction.  With no updates
     applied (cap 0) a substep ends on its warm start, so with a network of constant output
-    c the multipliers after three substeps are, per row, b^3 l_init plus c m g h^2 times
-    b^2 (substep 0), b (substep 1) and 1 (substep 2) for each substep s with
-    s % net_every == 0, on the predicted kinds only (all six; stretch, yaw, pitch; or
-    stretch)."""
+    c a row's multiplier after three substeps is m_2 m_1 m_0 l_init plus c m g h^2 times
+    m_2 m_1 (substep 0), m_2 (substep 1) and 1 (substep 2) for each network substep
+    (s % net_every == 0), where m_s = beta_net at a network substep on the predicted kinds
+    (all six; stretch, yaw, pitch; or stretch) and beta otherwise (beta_net unset: beta)."""
     w = W.batched(n=3, seed=13, links=(1, 3))
     s = W.solver_settings(iters=10, n_sub=3)
     o = oracle.OracleSim(w, s)
     o.step(2)
     c, b = 0.375, 0.5
+    bn = b if beta_net is None else beta_net
     p = np.zeros(M.N_PARAMS)
     p[-1] = c
-    o.set_cfg(iters=0, warm=2, beta=b, net_rows=net_rows, net_every=net_every)
+    o.set_cfg(iters=0, warm=2, beta=b, net_rows=net_rows, net_every=net_every,
+              beta_net=-1.0 if beta_net is None else beta_net)
     lam0 = o.lam.copy()
     o.step(1, mlp=p)
     h = s["dt"] / 3
     sc = np.repeat(w["mass"] * 9.81 * h * h, W.n_nodes(w))[:, None]
-    weight = sum(b ** (2 - k) for k in range(3) if k % net_every == 0)
     pred = {0: np.ones((1, 6)), 1: np.array([[1, 1, 1, 0, 0, 0]]), 2: np.array([[1, 0, 0, 0, 0, 0]])}[net_rows]
-    expect = b ** 3 * lam0 + c * weight * sc * pred
+    net = [k % net_every == 0 for k in range(3)]
+    m = [bn if net[k] else b for k in range(3)]  # factor of a predicted row at substep k
+    lin = m[0] * m[1] * m[2]
+    add = sum(np.prod(m[k + 1:]) for k in range(3) if net[k])
+    expect = np.where(pred > 0, lin * lam0 + c * add * sc, b ** 3 * lam0)
     # rows that do not exist stay zero (the chain's ends)
     F = o.features()
     exists = np.abs(F[:, :6]).sum(1).reshape(-1, 6) > 0

@@ -45,7 +45,7 @@ DEFAULTS = dict(
 def solver_settings(dt=1.0 / 60.0, n_sub=20, iters=10, tol=0.0, omega=1.0 / 3.0,
                     gravity=(0.0, 0.0, -9.81), contact=True, warm=0, beta=1.0, latency=0,
                     k_inflate=0.23, k_deflate=0.23, t_p=0.68 / 8.0, p_source=1.0, law_dt=0.0083,
-                    solver=0, pcr_iters=20, net_rows=0, net_every=1):
+                    solver=0, pcr_iters=20, net_rows=0, net_every=1, beta_net=-1.0):
     """Global settings: env-step dt, substeps, iteration cap, residual tolerance
     (0 = run exactly `iters` updates), Jacobi relaxation, gravity, ground contact on/off,
     warm start (0 = cold, 1 = beta x previous substep's multipliers, 2 = that plus the
@@ -58,15 +58,16 @@ def solver_settings(dt=1.0 / 60.0, n_sub=20, iters=10, tol=0.0, omega=1.0 / 3.0,
     preconditioned conjugate residual iterations, Sec. IV-D, `iters` capping the
     matrix-vector products; contact-free only); for the learned warm start, the row kinds
     the network predicts (net_rows 0 = all six, 1 = stretch, yaw and pitch only, 2 = stretch
-    only) and every
-    how many substeps it runs (net_every; the substeps in between start from beta x the
-    previous multipliers)."""
+    only), every how many substeps it runs (net_every; the substeps in between start from
+    beta x the previous multipliers) and the weight of the previous multipliers under its
+    prediction (beta_net; negative: beta)."""
     return dict(dt=float(dt), n_sub=int(n_sub), iters=int(iters), tol=float(tol),
                 omega=float(omega), gravity=tuple(float(g) for g in gravity),
                 contact=bool(contact), warm=int(warm), beta=float(beta), latency=int(latency),
                 k_inflate=float(k_inflate), k_deflate=float(k_deflate), t_p=float(t_p),
                 p_source=float(p_source), law_dt=float(law_dt), solver=int(solver),
-                pcr_iters=int(pcr_iters), net_rows=int(net_rows), net_every=int(net_every))
+                pcr_iters=int(pcr_iters), net_rows=int(net_rows), net_every=int(net_every),
+                beta_net=float(beta_net))
 
 
 def _base(n: int) -> dict:
