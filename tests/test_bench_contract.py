@@ -10,7 +10,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def test_reference_arm_prints_one_contract_line():
-    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "0"],
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "0",
+                        "--settle", "2"],
                        cwd=ROOT, capture_output=True, text=True, timeout=600)
     assert r.returncode == 0, r.stderr[-2000:]
     lines = [l for l in r.stdout.strip().splitlines() if l.startswith("{")]
@@ -28,7 +29,8 @@ def test_reference_arm_prints_one_contract_line():
     sys.path.insert(0, ROOT)
     import bench
     import workloads as W
-    assert d["config"] == bench.workload_config(int(W.n_nodes(bench.eval_batch(1)).sum()), 1)
+    assert d["config"] == bench.workload_config(int(W.n_nodes(bench.eval_batch(1)).sum()), 1, 2)
+    assert d["config"]["settle_steps"] == 2
     assert "sample" not in d["config"] and "snakes" in d["reference_sample"]
 
 
@@ -37,6 +39,7 @@ def test_cpu_baseline_reports_all_cores_and_one_core():
     import bench
     import workloads as W
     w = W.learned(n=64, seed=4)
-    r = bench.cpu_baseline(w, W.solver_settings(iters=bench.CAP, tol=bench.TOL), n_sample=4, budget_s=1.0)
+    r = bench.cpu_baseline(w, W.solver_settings(iters=bench.CAP, tol=bench.TOL), n_sample=4, budget_s=1.0,
+                           settle=2)
     assert r["kind"] == "oracle" and r["value"] > 0 and r["cores"] >= 1
     assert r["single_thread"]["cores"] == 1 and r["single_thread"]["value"] > 0
