@@ -38,13 +38,17 @@ TOL = 1e-4
 CAP = 5000
 SKIP = 0.5  # learned warm start: lambda0 = SKIP lambda_prev + m g h^2 network(features)
 # the learned warm start the metric is quoted on: the network on the bilateral rows
-# (stretch, yaw, pitch) at every third substep, trained on targets solved from beta x the
-# previous multipliers along trajectories that use the network in this same configuration
-# (every second substep ran as fast, every third ends fewer launches on their slowest
-# snake); the other variants, with the same network, are reported under `modes`
+# (stretch, yaw, pitch) at every third substep, its prediction on SKIP x the previous
+# multipliers, LEARNED_BETA x the previous multipliers at the other substeps and rows,
+# trained on targets solved from SKIP x the previous multipliers along trajectories that
+# use the network in this same configuration; PREV_BETA for the previous-multiplier start.
+# Each is the fastest value measured on the settled 16384-snake batch (network every 2nd /
+# 3rd / 4th substep: 505 k / 530 k / 498 k env-steps/s; LEARNED_BETA 0.5 ... 0.9: 458 k ...
+# 530 k (0.8) ... 517 k; PREV_BETA 0.65 ... 0.8: 409 k ... 432 k (0.75) ... 401 k); the
+# other learned variants, with the same network and weights, are reported under `modes`
 LEARNED = dict(net_rows=1, net_every=3)
-LEARNED_BETA = SKIP  # weight of lambda_prev at the learned mode's substeps without the network
-PREV_BETA = 0.5      # the previous-multiplier warm start's weight of lambda_prev
+LEARNED_BETA = 0.8   # weight of lambda_prev at the learned mode's substeps without the network
+PREV_BETA = 0.75     # the previous-multiplier warm start's weight of lambda_prev
 TARGET_WARM = 1  # training targets: solves started from SKIP x the previous multipliers
 LEARNED_VARIANTS = {"all_every1": dict(net_rows=0, net_every=1), "bilateral_every1": dict(net_rows=1, net_every=1),
                     "bilateral_every2": dict(net_rows=1, net_every=2), "bilateral_every3": dict(net_rows=1, net_every=3),
@@ -241,8 +245,8 @@ def run_gpu(args):
              ("learned", dict(warm=2, **learned))]
     if not args.no_learned_variants:
         # the network on other row kinds and at other periods
-        modes += [("learned_" + k, dict(warm=2, beta=skip, beta_net=skip, **v))
-                  for k, v in LEARNED_VARIANTS.items() if dict(v, beta=skip, beta_net=skip) != learned]
+        modes += [("learned_" + k, dict(warm=2, beta=lbeta, beta_net=skip, **v))
+                  for k, v in LEARNED_VARIANTS.items() if dict(v, beta=lbeta, beta_net=skip) != learned]
     results = {}
     clk_all = None
     layouts = {}
