@@ -866,9 +866,9 @@ def main():
     ap.add_argument("--train-schedule", default="deploy", choices=["all", "deploy"],
                     help="row kinds and period of the network on the learned training trajectories: "
                          "every row and substep, or the timed configuration (--net-rows, --net-every)")
-    ap.add_argument("--pairing", type=int, default=None,
-                    help="updates per env-step from which a snake is stepped by a warp pair "
-                         "(0: never; default: the library's)")
+    ap.add_argument("--pairing", type=float, default=None,
+                    help="share of every 32-lane layout's most expensive snakes stepped by warp pairs "
+                         "(default: the library's)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default lane layouts instead of timing them per mode (sim_autotune)")
     ap.add_argument("--no-configs", action="store_true",

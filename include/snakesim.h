@@ -214,15 +214,13 @@ SimStatus sim_get_layout(SimHandle* h, int nodes, int32_t* lanes, int32_t* nodes
  * lanes * nodes_per_lane >= nodes).  Errors: SIM_EINVAL. */
 SimStatus sim_set_layout(SimHandle* h, int nodes, int lanes, int nodes_per_lane);
 
-/* Pairing threshold (default 8000; 0 switches pairing off): in the 32-lane Jacobi layouts
- * with two or more nodes per lane, a snake whose previous env-step took at least
- * min_updates Jacobi updates (to the scheduler's cost bins, 1/16 of an octave wide) is
- * stepped by two warps together with half the nodes per lane, so that a few slow snakes
- * do not set the length of a launch.  The decision depends on the snake's own history
- * alone: a snake's result does not depend on the batch, its order or the sharding.  A
- * paired snake's node sums are added in another order than unpaired (rounding-level
- * differences).  Errors: SIM_EINVAL (min_updates 1 or negative). */
-SimStatus sim_set_pairing(SimHandle* h, int min_updates);
+/* Share (0..1, default 0.02) of the work items of every 32-lane Jacobi layout with two or
+ * more nodes per lane that two warps step together, with half the nodes per lane: the
+ * most expensive snakes by the previous env-step's update counts (the head of the
+ * layout's queue), whose single-warp passes would set the length of a launch.  Changes
+ * the schedule only, not what a snake computes beyond the summation order of its node
+ * sums.  Errors: SIM_EINVAL (share outside [0, 1]). */
+SimStatus sim_set_pairing(SimHandle* h, float share);
 
 /* Captures sim_step(h, n_steps) in a CUDA graph on first use and replays it
  * afterwards (the graph is rebuilt when the configuration or layout changes). */

@@ -16,10 +16,9 @@ constexpr int layout_id(int G, int NPL) { return (G == 8 ? 0 : G == 16 ? 1 : 2) 
 constexpr int layout_lanes(int id) { return 8 << (id / 4); }
 constexpr int layout_npl(int id) { return id % 4 + 1; }
 constexpr int kNumLayouts = 12;
-// Default pairing threshold (sim_set_pairing): a snake of a 32-lane layout whose previous
-// env-step took at least this many Jacobi updates (to the scheduler's cost bins) is
-// stepped by a pair of warps with half the nodes per lane.
-constexpr int kDefaultPairMinUpdates = 8000;
+// Default share of a 32-lane layout's work items (the most expensive first) that pairs of
+// warps step with half the nodes per lane (sim_set_pairing).
+constexpr float kDefaultPairFrac = 0.02f;
 
 // Row kinds whose warm-start features are written: in the learned warm start the kinds
 // the network predicts (the first 6, 3 or 1 of stretch, yaw, pitch, contact, friction
@@ -90,8 +89,7 @@ struct SolverArgs {
   float beta_net;         // SIM_WARM_LEARNED: weight of lambda_prev under the prediction
   int span;               // split mode: substeps the launch finishes (the first one with the
                           // network's start, the others from beta lambda_prev)
-  const int* n_pair;      // [1] leading work items of the layout's queue run by warp pairs
-                          // (written by the scheduler; null: none)
+  int n_pair;             // leading work items of the layout's queue run by pairs of warps
 };
 
 // Calibration (adjoint) state of a simulator, defined in adjoint.cu.

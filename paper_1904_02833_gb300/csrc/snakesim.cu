@@ -66,12 +66,12 @@ namespace {
 #endif
 // Persistent: every warp takes the next work item (32/G snakes of one node count) from
 // the layout's counter in global memory until none is left.  In the 32-lane Jacobi
-// layouts with two or more nodes per lane the first *A.n_pair items of the queue (the
-// snakes whose previous env-step reached the pairing threshold; the queue is ordered by
-// cost, so they come first) are taken by pairs of warps, warps 0 + 1 and 2 + 3 of a
-// block, which step the snake with half the nodes per lane (a launch lasts as long as
-// its slowest snake); the item that ends a pair's share is run by the pair's first warp
-// alone, and from there on every warp takes items alone.
+// layouts with two or more nodes per lane the first A.n_pair items of the queue (the
+// most expensive snakes of the previous env-step: the queue is ordered that way) are
+// taken by pairs of warps, warps 0 + 1 and 2 + 3 of a block, which step the snake with
+// half the nodes per lane (its slowest snakes set the length of a launch); the item that
+// ends a pair's share is run by the pair's first warp alone, and from there on every
+// warp takes items alone.
 template <int NPL, int G, int VAR>
 constexpr bool kPairs = G == 32 && NPL >= 2 && VAR != kVarPcr;
 template <int NPL, int G, bool SPLIT, int VAR>
@@ -83,8 +83,7 @@ __global__ void __launch_bounds__(128, SNAKE_MIN_BLOCKS) snake_solver_kernel(Sol
   if constexpr (kPairs<NPL, G, VAR>) {
     __shared__ float pair_buf[2][2 * 2 * kPairSlot];
     __shared__ int pair_item[2];
-    const int n_pair = A.n_pair ? *A.n_pair : 0;  // written by the scheduler before the launch
-    if (n_pair > 0) {  // the same value in every block
+    if (A.n_pair > 0) {  // a kernel argument: the same in every block
       const int warp = threadIdx.x >> 5, pair = warp >> 1;
       WarpPair P{pair_buf[pair], warp & 1, 1 + pair, 0};
       for (;;) {
@@ -92,7 +91,7 @@ __global__ void __launch_bounds__(128, SNAKE_MIN_BLOCKS) snake_solver_kernel(Sol
         pair_sync(P);
         it = pair_item[pair];
         pair_sync(P);  // both warps have read it before the next fetch writes it
-        if (it >= n_pair) break;
+        if (it >= A.n_pair) break;
         run_group<(NPL + 1) / 2, 32, SPLIT, VAR, 2>(A, A.order[A.items[it].x], true, solver_smem, &P);
       }
       have = (warp & 1) == 0;
@@ -148,8 +147,6 @@ struct SchedArgs {
   int* key;             // [n_items] scratch
   int* order;           // out: the snakes of class c at [cls_base[c], cls_base[c] + count)
   int4* items;          // out: the queue of layout l at [lay_first[l], lay_first[l + 1])
-  int* n_pair;           // out: [12] items at the head of each layout's queue for warp pairs
-  int pair_bin;          // cost bin at or above which a snake is paired (-1: none)
   int n, n_cls, n_items;
   int lay_first[12];
 };
@@ -166,12 +163,6 @@ __device__ __forceinline__ int sched_bin(int v) {
   const int e = 31 - __clz(v);
   const int m = e >= 4 ? (v >> (e - 4)) & 15 : (v << (4 - e)) & 15;
   return 255 - min(255, 16 * e + m);
-}
-int sched_bin_host(int v) {
-  v = std::max(v, 1);
-  const int e = 31 - __builtin_clz((unsigned)v);
-  const int m = e >= 4 ? (v >> (e - 4)) & 15 : (v << (4 - e)) & 15;
-  return 255 - std::min(255, 16 * e + m);
 }
 
 // In-place exclusive prefix sum of 256 counters by one warp.
@@ -218,11 +209,6 @@ __global__ void __launch_bounds__(1024) schedule_kernel(SchedArgs a) {
   }
   __syncthreads();
   for (int r = warp; r < 12; r += nw) warp_scan256(hi + r * 256);
-  __syncthreads();
-  // the head of each layout's queue that warp pairs take: the items whose cost bin is at
-  // or above the pairing bin (the queue is ordered by bin, so they come first); whether a
-  // snake is paired depends on its own last update count alone
-  if (t < 12) a.n_pair[t] = a.pair_bin >= 0 ? hi[t * 256 + a.pair_bin + 1] : 0;
   __syncthreads();
   for (int k = t; k < a.n_items; k += T) {
     const int4 it = a.items0[k];
@@ -282,8 +268,7 @@ __global__ void training_rows_kernel(const __nv_bfloat16* __restrict__ feat, con
 // ------------------------------------------------------------------ handle
 struct SimHandle {
   SimConfig cfg;
-  int pair_min = kDefaultPairMinUpdates;  // pairing threshold (updates per env-step; 0: off)
-  int* n_pair_d = nullptr;                // [12] written by the scheduler
+  float pair_frac = kDefaultPairFrac;  // share of a layout's work items run by warp pairs
   int n = 0;
   long long n_nodes = 0, n_links = 0;
   cudaStream_t stream = nullptr;
@@ -541,7 +526,7 @@ SolverArgs make_args(SimHandle* h, int n_steps) {
   A.feat_kinds = feature_kinds(h->cfg.warm, h->cfg.net_rows);
   A.beta_net = h->cfg.beta_net < 0.f ? h->cfg.beta : h->cfg.beta_net;
   A.span = 1;
-  A.n_pair = nullptr;  // per layout (launch_layout)
+  A.n_pair = 0;  // per layout (launch_layout)
   return A;
 }
 
@@ -578,8 +563,6 @@ SimStatus schedule(SimHandle* h, cudaStream_t st) {
   a.iters = h->iters; a.node_off = h->node_off_d; a.cls = h->sched_cls; a.cls_base = h->sched_base;
   a.items0 = h->items0; a.hist = h->sched_hist; a.key = h->sched_key; a.order = h->order;
   a.items = h->items; a.n = h->n; a.n_cls = h->n_cls; a.n_items = h->n_items;
-  a.n_pair = h->n_pair_d;
-  a.pair_bin = h->pair_min > 0 ? sched_bin_host(h->pair_min) : -1;  // <= 239 for pair_min >= 2
   for (int l = 0; l < kLayouts; ++l) a.lay_first[l] = h->lay_first[l];
   schedule_kernel<<<1, 1024, 0, st>>>(a);
   CU(cudaGetLastError());
@@ -645,7 +628,9 @@ SimStatus launch_layout(SimHandle* h, const SolverArgs& A, int l, cudaStream_t s
   B.items = h->items + h->lay_first[l];
   B.n_items = h->lay_first[l + 1] - h->lay_first[l];
   B.work = h->work + l;
-  B.n_pair = h->n_pair_d + l;
+  const int var_l = solver_var(h);
+  B.n_pair = (var_l != kVarPcr && layout_lanes(l) == 32 && layout_npl(l) >= 2)
+                 ? (int)std::ceil((double)h->pair_frac * B.n_items) : 0;
   CU(cudaMemsetAsync(B.work, 0, sizeof(int), s));
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   CU(cudaStreamIsCapturing(s, &cap));
@@ -789,7 +774,6 @@ SimStatus sim_create(const SimConfig* cfg, int n_snakes, const SnakeParams* para
   ALLOC(h->step_dev, sizeof(long long));
   ALLOC(h->work, kLayouts * sizeof(int));
   ALLOC(h->feat, h->n_nodes * 6 * 32 * sizeof(__nv_bfloat16));
-  ALLOC(h->n_pair_d, kLayouts * sizeof(int));
 #undef ALLOC
 #define CUC(call)                                                                         \
   e = (call);                                                                             \
@@ -799,7 +783,6 @@ SimStatus sim_create(const SimConfig* cfg, int n_snakes, const SnakeParams* para
   CUC(cudaMemset(h->press, 0, h->n_links * sizeof(float2)));
   CUC(cudaMemset(h->lam, 0, h->n_nodes * 6 * sizeof(float)));
   CUC(cudaMemset(h->feat, 0, h->n_nodes * 6 * 32 * sizeof(__nv_bfloat16)));
-  CUC(cudaMemset(h->n_pair_d, 0, kLayouts * sizeof(int)));
   CUC(cudaMemcpy(h->prm, params, n_snakes * sizeof(SnakeParams), cudaMemcpyHostToDevice));
   CUC(cudaMemcpy(h->node_off_d, h->node_off.data(), (n_snakes + 1) * sizeof(int), cudaMemcpyHostToDevice));
   CUC(cudaMemcpy(h->link_off_d, h->link_off.data(), (n_snakes + 1) * sizeof(int), cudaMemcpyHostToDevice));
@@ -1011,10 +994,10 @@ SimStatus sim_set_layout(SimHandle* h, int nodes, int lanes, int npl) {
   return build_items(h);
 }
 
-SimStatus sim_set_pairing(SimHandle* h, int min_updates) {
+SimStatus sim_set_pairing(SimHandle* h, float frac) {
   if (!h) return fail(SIM_EINVAL, "null handle");
-  if (min_updates < 0 || min_updates == 1) return fail(SIM_EINVAL, "pairing threshold must be 0 or >= 2");
-  h->pair_min = min_updates;
+  if (!(frac >= 0.f && frac <= 1.f)) return fail(SIM_EINVAL, "pairing share outside [0, 1]");
+  h->pair_frac = frac;
   h->graph_dirty = true;
   return SIM_OK;
 }
@@ -1347,7 +1330,7 @@ SimStatus sim_destroy(SimHandle* h) {
                   h->lam0, h->feat, h->snap_pos, h->snap_vel, h->snap_press, h->snap_lam,
                   h->step_dev, h->snap_step_dev, h->work, h->sched_cls, h->sched_base,
                   h->sched_hist, h->sched_key, h->items0, h->feat_off_d, h->snap_resid,
-                  h->snap_iters, h->snap_status, h->snap_feat, h->train_off, h->n_pair_d};
+                  h->snap_iters, h->snap_status, h->snap_feat, h->train_off};
   for (void* p : ptrs) if (p) cudaFree(p);
   delete h;
   return SIM_OK;
