@@ -156,10 +156,9 @@ def test_warp_pairs_match_oracle(share):
     values through shared memory): every 32-lane layout with two or more nodes per lane
     (33-128 nodes), all of a layout's work items paired or the head of its queue only
     (pairs, then single warps in the same launch); fixed update counts, a tolerance with
-    the previous multipliers (on the benchmark's 41-81-node snakes, where the tolerance
-    stop's velocity floor was established), anisotropic friction, and the learned warm
-    start's split launches, against the oracle; and against the same run without pairs
-    (the node sums of a snake differ only in their summation order)."""
+    the previous multipliers, anisotropic friction, and the learned warm start's split
+    launches, against the oracle; and against the same run without pairs (the node sums
+    of a snake differ only in their summation order)."""
     from oracle import mlp_oracle as M
     from paper_1904_02833_gb300.mlp import WarmStartMLP
     w = W.batched(n=24, seed=43, links=(1, 12))
@@ -169,14 +168,12 @@ def test_warp_pairs_match_oracle(share):
     assert nodes.max() <= 128 and (nodes > 32).sum() >= 12
     p = M.init_params(12) * 0.5
     net = WarmStartMLP(p)
-    w81 = W.batched(n=24, seed=44, links=(4, 8))
-    cases = [(w, W.solver_settings(iters=10), {}),
-             (w81, W.solver_settings(iters=5000, tol=1e-4, warm=1, beta=0.75), {}),
-             (w, W.solver_settings(iters=10), {"mu_side": 0.25}),
-             (w, W.solver_settings(iters=10, warm=2, beta=0.8, beta_net=0.5, net_rows=1, net_every=3), {})]
-    for wb, s, extra in cases:
-        wc = dict(wb)
-        nodes = W.n_nodes(wc)
+    cases = [(W.solver_settings(iters=10), {}),
+             (W.solver_settings(iters=5000, tol=1e-4, warm=1, beta=0.75), {}),
+             (W.solver_settings(iters=10), {"mu_side": 0.25}),
+             (W.solver_settings(iters=10, warm=2, beta=0.8, beta_net=0.5, net_rows=1, net_every=3), {})]
+    for s, extra in cases:
+        wc = dict(w)
         for k, v in extra.items():
             wc[k] = np.where(nodes > 32, v, 0.0)
         runs = []
