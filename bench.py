@@ -232,8 +232,6 @@ def run_gpu(args):
     total_links = int(w["n_links"].sum())
     alu_peak, alu_peak_source = device_alu_peak(local)
     sim = SnakeSim(w, W.solver_settings(iters=CAP, tol=TOL, warm=W_COLD))
-    if args.pairing is not None:
-        sim.set_pairing(args.pairing)
     sim.set_mlp(net)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
@@ -866,9 +864,6 @@ def main():
     ap.add_argument("--train-schedule", default="deploy", choices=["all", "deploy"],
                     help="row kinds and period of the network on the learned training trajectories: "
                          "every row and substep, or the timed configuration (--net-rows, --net-every)")
-    ap.add_argument("--pairing", type=float, default=None,
-                    help="share of every 32-lane layout's most expensive snakes stepped by warp pairs "
-                         "(default: the library's)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default lane layouts instead of timing them per mode (sim_autotune)")
     ap.add_argument("--no-configs", action="store_true",

@@ -214,14 +214,6 @@ SimStatus sim_get_layout(SimHandle* h, int nodes, int32_t* lanes, int32_t* nodes
  * lanes * nodes_per_lane >= nodes).  Errors: SIM_EINVAL. */
 SimStatus sim_set_layout(SimHandle* h, int nodes, int lanes, int nodes_per_lane);
 
-/* Share (0..1, default 0.02) of the work items of every 32-lane Jacobi layout with two or
- * more nodes per lane that two warps step together, with half the nodes per lane: the
- * most expensive snakes by the previous env-step's update counts (the head of the
- * layout's queue), whose single-warp passes would set the length of a launch.  Changes
- * the schedule only, not what a snake computes beyond the summation order of its node
- * sums.  Errors: SIM_EINVAL (share outside [0, 1]). */
-SimStatus sim_set_pairing(SimHandle* h, float share);
-
 /* Captures sim_step(h, n_steps) in a CUDA graph on first use and replays it
  * afterwards (the graph is rebuilt when the configuration or layout changes). */
 SimStatus sim_step_graph(SimHandle* h, int n_steps);
@@ -383,8 +375,7 @@ SimStatus sim_feature_offsets(SimHandle* h, int32_t* first_row);
 
 /* Training rows of the learned warm start, for the substep in progress of split stepping
  * (after sim_split_begin, before the sim_split_finish that completes it).  The network's
- * output y enters the warm start as lambda0 = beta lambda_prev + m g h^2 y (beta: the
- * configuration's beta_net, the weight under the prediction), so the
+ * output y enters the warm start as lambda0 = beta lambda_prev + m g h^2 y, so the
  * target that makes the warm start land on a reference solution lambda_star is
  *   y* = (lambda_star - beta lambda_prev) / (m g h^2)
  * with m the snake's node mass, g = 9.81 m/s^2 and h = dt / n_sub of the current

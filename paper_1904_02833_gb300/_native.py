@@ -87,7 +87,6 @@ SIGNATURES = {
     "sim_autotune": [H, ctypes.c_int],
     "sim_get_layout": [H, ctypes.c_int, I32P, I32P],
     "sim_set_layout": [H, ctypes.c_int, ctypes.c_int, ctypes.c_int],
-    "sim_set_pairing": [H, ctypes.c_float],
     "sim_launch_count": [H, I64P],
     "sim_kernel_timing": [H, ctypes.c_int],
     "sim_feature_offsets": [H, P],

@@ -16,9 +16,6 @@ constexpr int layout_id(int G, int NPL) { return (G == 8 ? 0 : G == 16 ? 1 : 2) 
 constexpr int layout_lanes(int id) { return 8 << (id / 4); }
 constexpr int layout_npl(int id) { return id % 4 + 1; }
 constexpr int kNumLayouts = 12;
-// Default share of a 32-lane layout's work items (the most expensive first) that pairs of
-// warps step with half the nodes per lane (sim_set_pairing).
-constexpr float kDefaultPairFrac = 0.02f;
 
 // Row kinds whose warm-start features are written: in the learned warm start the kinds
 // the network predicts (the first 6, 3 or 1 of stretch, yaw, pitch, contact, friction
@@ -89,7 +86,6 @@ struct SolverArgs {
   float beta_net;         // SIM_WARM_LEARNED: weight of lambda_prev under the prediction
   int span;               // split mode: substeps the launch finishes (the first one with the
                           // network's start, the others from beta lambda_prev)
-  int n_pair;             // leading work items of the layout's queue run by pairs of warps
 };
 
 // Calibration (adjoint) state of a simulator, defined in adjoint.cu.

@@ -65,44 +65,15 @@ namespace {
 #define SNAKE_MIN_BLOCKS 2
 #endif
 // Persistent: every warp takes the next work item (32/G snakes of one node count) from
-// the layout's counter in global memory until none is left.  In the 32-lane Jacobi
-// layouts with two or more nodes per lane the first A.n_pair items of the queue (the
-// most expensive snakes of the previous env-step: the queue is ordered that way) are
-// taken by pairs of warps, warps 0 + 1 and 2 + 3 of a block, which step the snake with
-// half the nodes per lane (its slowest snakes set the length of a launch); the item that
-// ends a pair's share is run by the pair's first warp alone, and from there on every
-// warp takes items alone.
-template <int NPL, int G, int VAR>
-constexpr bool kPairs = G == 32 && NPL >= 2 && VAR != kVarPcr;
+// the layout's counter in global memory until none is left.
 template <int NPL, int G, bool SPLIT, int VAR>
 __global__ void __launch_bounds__(128, SNAKE_MIN_BLOCKS) snake_solver_kernel(SolverArgs A) {
   extern __shared__ float solver_smem[];  // Newton + PCR only (kPcrFloatsPerSlot x 32 NPL per warp)
   const int lane = threadIdx.x & 31;
-  int it = 0;
-  bool have = false;  // `it` holds an item this warp runs alone
-  if constexpr (kPairs<NPL, G, VAR>) {
-    __shared__ float pair_buf[2][2 * 2 * kPairSlot];
-    __shared__ int pair_item[2];
-    if (A.n_pair > 0) {  // a kernel argument: the same in every block
-      const int warp = threadIdx.x >> 5, pair = warp >> 1;
-      WarpPair P{pair_buf[pair], warp & 1, 1 + pair, 0};
-      for (;;) {
-        if ((threadIdx.x & 63) == 0) pair_item[pair] = atomicAdd(A.work, 1);
-        pair_sync(P);
-        it = pair_item[pair];
-        pair_sync(P);  // both warps have read it before the next fetch writes it
-        if (it >= A.n_pair) break;
-        run_group<(NPL + 1) / 2, 32, SPLIT, VAR, 2>(A, A.order[A.items[it].x], true, solver_smem, &P);
-      }
-      have = (warp & 1) == 0;
-    }
-  }
   for (;;) {
-    if (!have) {
-      if (lane == 0) it = atomicAdd(A.work, 1);
-      it = __shfl_sync(0xffffffffu, it, 0);
-    }
-    have = false;
+    int it = 0;
+    if (lane == 0) it = atomicAdd(A.work, 1);
+    it = __shfl_sync(0xffffffffu, it, 0);
     if (it >= A.n_items) break;
     const int4 item = A.items[it];
     const int gi = lane / G;
@@ -268,7 +239,6 @@ __global__ void training_rows_kernel(const __nv_bfloat16* __restrict__ feat, con
 // ------------------------------------------------------------------ handle
 struct SimHandle {
   SimConfig cfg;
-  float pair_frac = kDefaultPairFrac;  // share of a layout's work items run by warp pairs
   int n = 0;
   long long n_nodes = 0, n_links = 0;
   cudaStream_t stream = nullptr;
@@ -526,7 +496,6 @@ SolverArgs make_args(SimHandle* h, int n_steps) {
   A.feat_kinds = feature_kinds(h->cfg.warm, h->cfg.net_rows);
   A.beta_net = h->cfg.beta_net < 0.f ? h->cfg.beta : h->cfg.beta_net;
   A.span = 1;
-  A.n_pair = 0;  // per layout (launch_layout)
   return A;
 }
 
@@ -628,9 +597,6 @@ SimStatus launch_layout(SimHandle* h, const SolverArgs& A, int l, cudaStream_t s
   B.items = h->items + h->lay_first[l];
   B.n_items = h->lay_first[l + 1] - h->lay_first[l];
   B.work = h->work + l;
-  const int var_l = solver_var(h);
-  B.n_pair = (var_l != kVarPcr && layout_lanes(l) == 32 && layout_npl(l) >= 2)
-                 ? (int)std::ceil((double)h->pair_frac * B.n_items) : 0;
   CU(cudaMemsetAsync(B.work, 0, sizeof(int), s));
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   CU(cudaStreamIsCapturing(s, &cap));
@@ -992,14 +958,6 @@ SimStatus sim_set_layout(SimHandle* h, int nodes, int lanes, int npl) {
     return fail(SIM_EINVAL, "layout needs lanes in {8,16,32}, nodes_per_lane in 1..4, lanes*npl >= nodes");
   h->layout[nodes] = layout_id(lanes, npl);
   return build_items(h);
-}
-
-SimStatus sim_set_pairing(SimHandle* h, float frac) {
-  if (!h) return fail(SIM_EINVAL, "null handle");
-  if (!(frac >= 0.f && frac <= 1.f)) return fail(SIM_EINVAL, "pairing share outside [0, 1]");
-  h->pair_frac = frac;
-  h->graph_dirty = true;
-  return SIM_OK;
 }
 
 SimStatus sim_autotune(SimHandle* h, int n_steps) {

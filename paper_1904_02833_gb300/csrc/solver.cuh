@@ -113,79 +113,6 @@ __device__ __forceinline__ float group_max(float r) {
   return r;
 }
 
-// Two warps of one block that step one snake together (W = 2: lane q of the group is
-// 32 x the warp's position in the pair + its lane).  Values cross the warp boundary
-// through a small shared-memory area with one named barrier per exchange; the area is
-// double-buffered, so that a slot is written again only after both warps have passed
-// the barrier that follows its reads.  Every exchange is reached by both warps the same
-// number of times: the group's control flow (substeps, the stop decision, the work item)
-// is the same in both.
-constexpr int kPairSlot = 12;  // floats per warp and slot: up to 9 boundary values, 1 scalar
-struct WarpPair {
-  float* buf;  // [2 slots][2 warps][kPairSlot]
-  int pw;      // the warp's position in the pair
-  int bar;     // named barrier id (1 + the pair's index in the block)
-  int slot;    // the slot the next exchange uses
-};
-
-__device__ __forceinline__ void pair_sync(const WarpPair& P) {
-  asm volatile("bar.sync %0, 64;" ::"r"(P.bar) : "memory");
-}
-
-// Neighbour values in the group: from_l[k] = up[k] of lane q - 1, from_r[k] = dn[k] of
-// lane q + 1 (shuffles of width G; with W = 2 the two lanes at the warp boundary through
-// shared memory).  W = 2 also swaps a per-warp scalar (`mine`, any lane's value) and
-// returns the other warp's; W = 1 returns 0.  The group's first and last lane receive
-// their own values (unused: there is no node beyond them).
-template <int G, int W, int N>
-__device__ __forceinline__ float group_neighbours(WarpPair* P, const float (&up)[N], const float (&dn)[N],
-                                                  float (&from_l)[N], float (&from_r)[N], float mine = 0.f) {
-#pragma unroll
-  for (int k = 0; k < N; ++k) {
-    from_l[k] = __shfl_up_sync(kFull, up[k], 1, G);
-    from_r[k] = __shfl_down_sync(kFull, dn[k], 1, G);
-  }
-  float other = 0.f;
-  if constexpr (W == 2) {
-    static_assert(N <= kPairSlot - 1, "exchange area too small");
-    const int lane = threadIdx.x & 31;
-    float* s = P->buf + P->slot * 2 * kPairSlot;
-    P->slot ^= 1;
-    if (P->pw == 0 && lane == 31) {
-#pragma unroll
-      for (int k = 0; k < N; ++k) s[k] = up[k];
-    }
-    if (P->pw == 1 && lane == 0) {
-#pragma unroll
-      for (int k = 0; k < N; ++k) s[kPairSlot + k] = dn[k];
-    }
-    if (lane == 0) s[P->pw * kPairSlot + kPairSlot - 1] = mine;
-    pair_sync(*P);
-    if (P->pw == 1 && lane == 0) {
-#pragma unroll
-      for (int k = 0; k < N; ++k) from_l[k] = s[k];
-    }
-    if (P->pw == 0 && lane == 31) {
-#pragma unroll
-      for (int k = 0; k < N; ++k) from_r[k] = s[kPairSlot + k];
-    }
-    other = s[(1 - P->pw) * kPairSlot + kPairSlot - 1];
-  }
-  return other;
-}
-
-// Max over the group's lanes.
-template <int G, int W>
-__device__ __forceinline__ float group_max_w(WarpPair* P, float r) {
-  r = group_max<G>(r);
-  if constexpr (W == 2) {
-    const float none[1] = {0.f};
-    float a[1], b[1];
-    r = fmaxf(r, group_neighbours<G, 2, 1>(P, none, none, a, b, r));
-  }
-  return r;
-}
-
 // Per-group constants of one snake.
 struct SnakeK {
   int N, seg, nfix, L, nb, lb, fb;  // fb: first node of the snake in the feature row order
@@ -235,16 +162,20 @@ namespace snakesim {
 // (on a straight dummy segment where the segment does not exist) and a row that does not
 // exist contributes d = 0 and residual 0, so that the lane's node slots form independent
 // instruction streams the scheduler can interleave.
-template <int NPL, int G, bool WARM, bool ANISO, int W = 1>
+template <int NPL, int G, bool WARM, bool ANISO>
 __device__ __forceinline__ float row_pass(const SnakeK& S, const SolverArgs& A, int q,
                                           bool live, int kiter, const float (&xs)[NPL][3],
                                           float (&dx)[NPL][3], const float (&xsl)[3],
                                           const float (&xsr)[3], float (&lam)[NPL][6],
-                                          const float (&th)[NPL], bool& stop, WarpPair* P = nullptr) {
+                                          const float (&th)[NPL], bool& stop) {
   const float L0 = S.L0;
   // neighbour displacements across the lane boundary
   float dxl[3], dxr[3];
-  group_neighbours<G, W, 3>(P, dx[NPL - 1], dx[0], dxl, dxr);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    dxl[d] = __shfl_up_sync(kFull, dx[NPL - 1][d], 1, G);
+    dxr[d] = __shfl_down_sync(kFull, dx[0][d], 1, G);
+  }
   const int i0 = q * NPL;
   // segment i (from node i to node i + 1) from its two end nodes; a straight dummy where
   // the segment does not exist
@@ -419,22 +350,22 @@ __device__ __forceinline__ float row_pass(const SnakeK& S, const SolverArgs& A, 
     // every term is a length: one scaling by 1 / L0 (monotone, so the max is the same)
     r = fmaxf(r, sqrtf(q2)) * S.inv_L0;
     if (!(r <= 3.0e38f)) r = INFINITY;  // NaN -> inf so that the max keeps it
-  }
-  // contributions that cross lane boundaries: the left lane's rows to my first node
-  // (fromL), the right lane's rows to my last node (fromR); with two warps the same
-  // exchange carries each warp's "some lane over the tolerance"
-  float fromR[3], fromL[3];
-  const unsigned over = WARM ? 0u : __ballot_sync(kFull, !(r <= A.tol));
-  const float other_over = group_neighbours<G, W, 3>(P, accR, accL, fromL, fromR, over != 0u ? 1.f : 0.f);
-  if (!WARM) {
     // one ballot decides every group's stop; the group's max residual is reduced only in
     // the (rare) passes where some live group stops, to be recorded
     const unsigned lane = threadIdx.x & 31u;
+    const unsigned over = __ballot_sync(kFull, !(r <= A.tol));
     const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(unsigned)(G - 1)));
-    stop = ((over & gmask) == 0u && other_over == 0.f) || (kiter >= A.K);
-    if (__any_sync(kFull, stop && live)) r = group_max_w<G, W>(P, r);
+    stop = ((over & gmask) == 0u) || (kiter >= A.K);
+    if (__any_sync(kFull, stop && live)) r = group_max<G>(r);
   } else {
     stop = false;
+  }
+  // contributions that cross lane boundaries
+  float fromR[3], fromL[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    fromR[d] = __shfl_down_sync(kFull, accL[d], 1, G);  // right lane's rows -> my last node
+    fromL[d] = __shfl_up_sync(kFull, accR[d], 1, G);    // left lane's rows -> my first node
   }
   // update, by selects: a node slot beyond the snake or a group that stops keeps its state
   const bool upd = live && !stop;
@@ -443,7 +374,7 @@ __device__ __forceinline__ float row_pass(const SnakeK& S, const SolverArgs& A, 
     const int i = i0 + j;
     float ax = acc[j][0], ay = acc[j][1], az = acc[j][2];
     if (j == 0 && q > 0) { ax += fromL[0]; ay += fromL[1]; az += fromL[2]; }
-    if (j == NPL - 1 && q < G * W - 1) { ax += fromR[0]; ay += fromR[1]; az += fromR[2]; }
+    if (j == NPL - 1 && q < G - 1) { ax += fromR[0]; ay += fromR[1]; az += fromR[2]; }
     const bool on = upd && i < S.N;
     const float wi = (i < S.nfix) ? 0.f : S.inv_m;
     dx[j][0] = on ? dx[j][0] + wi * ax : dx[j][0];
@@ -464,20 +395,20 @@ __device__ __forceinline__ float row_pass(const SnakeK& S, const SolverArgs& A, 
 // three nodes in the frame, x h / L0 (9); rest angle of a yaw row (1); the row's
 // multiplier from the previous substep / (m g h^2) (1).  Rows that do not exist are zero;
 // only the first A.feat_kinds kinds are written (the kinds the network predicts).
-template <int NPL, int G, int W = 1>
+template <int NPL, int G>
 __device__ __forceinline__ void write_features(const SnakeK& S, const SolverArgs& A, int q, bool valid,
                                                const float (&xs)[NPL][3], const float (&dx)[NPL][3],
                                                const float (&v)[NPL][3], const float (&lam)[NPL][6],
-                                               const float (&th)[NPL], WarpPair* P = nullptr) {
+                                               const float (&th)[NPL]) {
   float nl[9], nr[9];  // left / right neighbour: xs, dx, v
-  {
-    float up[9], dn[9];
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      up[d] = xs[NPL - 1][d]; up[3 + d] = dx[NPL - 1][d]; up[6 + d] = v[NPL - 1][d];
-      dn[d] = xs[0][d]; dn[3 + d] = dx[0][d]; dn[6 + d] = v[0][d];
-    }
-    group_neighbours<G, W, 9>(P, up, dn, nl, nr);
+  for (int d = 0; d < 3; ++d) {
+    nl[d] = __shfl_up_sync(kFull, xs[NPL - 1][d], 1, G);
+    nl[3 + d] = __shfl_up_sync(kFull, dx[NPL - 1][d], 1, G);
+    nl[6 + d] = __shfl_up_sync(kFull, v[NPL - 1][d], 1, G);
+    nr[d] = __shfl_down_sync(kFull, xs[0][d], 1, G);
+    nr[3 + d] = __shfl_down_sync(kFull, dx[0][d], 1, G);
+    nr[6 + d] = __shfl_down_sync(kFull, v[0][d], 1, G);
   }
   if (!valid) return;
   const float lsc = 1.0f / (S.mass * 9.81f * A.h * A.h);
@@ -737,12 +668,11 @@ __device__ void newton_pcr(const SnakeK& S, const SolverArgs& A, int q, bool val
 // preconditioned conjugate residual over the bilateral rows (contact-free substeps;
 // `smem` is its per-block shared-memory area).
 enum { kVarJacobi = 0, kVarAniso = 1, kVarPcr = 2 };
-template <int NPL, int G, bool SPLIT, int VAR, int W = 1>
-__device__ void run_group(const SolverArgs& A, int snake, bool valid, float* smem, WarpPair* WP = nullptr) {
+template <int NPL, int G, bool SPLIT, int VAR>
+__device__ void run_group(const SolverArgs& A, int snake, bool valid, float* smem) {
   constexpr bool ANISO = VAR == kVarAniso;
-  static_assert(W == 1 || (W == 2 && G == 32 && VAR != kVarPcr), "warp pairs: 32-lane Jacobi groups only");
   const int lane = threadIdx.x & 31;
-  const int q = (W == 2 ? WP->pw * 32 : 0) + (lane & (G - 1));
+  const int q = lane & (G - 1);
   SnakeK S;
   SnakeParams P;
   if (valid) P = A.prm[snake];
@@ -852,7 +782,11 @@ __device__ void run_group(const SolverArgs& A, int snake, bool valid, float* sme
   // warm start adds the network's prediction at this substep
   auto finish_substep = [&](float& rmax, int& itot, bool net) {
     float xsl[3], xsr[3];
-    group_neighbours<G, W, 3>(WP, xs[NPL - 1], xs[0], xsl, xsr);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      xsl[d] = __shfl_up_sync(kFull, xs[NPL - 1][d], 1, G);
+      xsr[d] = __shfl_down_sync(kFull, xs[0][d], 1, G);
+    }
     bool stop;
     if (A.warm == 0) {
 #pragma unroll
@@ -875,16 +809,16 @@ __device__ void run_group(const SolverArgs& A, int snake, bool valid, float* sme
           lam[j][k] = l;
         }
       }
-      row_pass<NPL, G, true, ANISO, W>(S, A, q, valid, 0, xs, dx, xsl, xsr, lam, th, stop, WP);
+      row_pass<NPL, G, true, ANISO>(S, A, q, valid, 0, xs, dx, xsl, xsr, lam, th, stop);
     }
     bool done = !valid;
     float rs = 0.f;
     int ks = 0;
-    if constexpr (VAR == kVarPcr) {
+    if (VAR == kVarPcr) {
       newton_pcr<NPL, G>(S, A, q, valid, xs, dx, lam, th, smem, rs, ks);
     } else {
       for (int k = 0;; ++k) {
-        const float r = row_pass<NPL, G, false, ANISO, W>(S, A, q, !done, k, xs, dx, xsl, xsr, lam, th, stop, WP);
+        const float r = row_pass<NPL, G, false, ANISO>(S, A, q, !done, k, xs, dx, xsl, xsr, lam, th, stop);
         if (!done && stop) { done = true; rs = r; ks = k; }
         if (__all_sync(kFull, done)) break;
       }
@@ -894,7 +828,7 @@ __device__ void run_group(const SolverArgs& A, int snake, bool valid, float* sme
 #pragma unroll
     for (int j = 0; j < NPL; ++j)
       if (!(fabsf(dx[j][0]) + fabsf(dx[j][1]) + fabsf(dx[j][2]) <= 3.0e38f)) bad = 1.f;
-    bad = group_max_w<G, W>(WP, bad);
+    bad = group_max<G>(bad);
     rmax = fmaxf(rmax, rs);
     if (!(rs <= 3.0e38f) || bad > 0.f) rmax = INFINITY;
     itot += ks;
@@ -936,7 +870,7 @@ __device__ void run_group(const SolverArgs& A, int snake, bool valid, float* sme
     }
     if (next < A.n_sub) {
       begin_substep(step0, next);
-      if (SPLIT) write_features<NPL, G, W>(S, A, q, valid, xs, dx, v, lam, th, WP);
+      if (SPLIT) write_features<NPL, G>(S, A, q, valid, xs, dx, v, lam, th);
       at_boundary = false;
     }
   }

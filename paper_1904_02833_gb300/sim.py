@@ -140,10 +140,6 @@ class SnakeSim:
     def set_layout(self, nodes: int, lanes: int, npl: int):
         N.check(self.lib.sim_set_layout(self.h, int(nodes), int(lanes), int(npl)))
 
-    def set_pairing(self, share: float):
-        """Share of every 32-lane layout's most expensive work items stepped by warp pairs."""
-        N.check(self.lib.sim_set_pairing(self.h, float(share)))
-
     @property
     def step_index(self) -> int:
         si = ctypes.c_int64()

@@ -73,7 +73,6 @@ def test_argument_validation_without_gpu(lib):
     assert lib.sim_create(ctypes.byref(cfg), 0, prm, None, ctypes.byref(h)) == N.SIM_EINVAL
     assert h.value is None
     assert b"n_snakes" in lib.sim_last_error()
-    assert lib.sim_set_pairing(None, 0.5) == N.SIM_EINVAL
     bad = make_params(W.single_snake())
     bad[0].mass = 0.0
     assert lib.sim_create(ctypes.byref(cfg), 1, bad, None, ctypes.byref(h)) == N.SIM_EINVAL

@@ -150,54 +150,6 @@ def test_every_layout_matches_oracle():
             g.close()
 
 
-@pytest.mark.parametrize("share", [1.0, 0.4])
-def test_warp_pairs_match_oracle(share):
-    """Snakes stepped by pairs of warps (two warps, half the nodes per lane, boundary
-    values through shared memory): every 32-lane layout with two or more nodes per lane
-    (33-128 nodes), all of a layout's work items paired or the head of its queue only
-    (pairs, then single warps in the same launch); fixed update counts, a tolerance with
-    the previous multipliers, anisotropic friction, and the learned warm start's split
-    launches, against the oracle; and against the same run without pairs (the node sums
-    of a snake differ only in their summation order)."""
-    from oracle import mlp_oracle as M
-    from paper_1904_02833_gb300.mlp import WarmStartMLP
-    w = W.batched(n=24, seed=43, links=(1, 12))
-    w["n_links"][:4] = [4, 8, 12, 6]
-    w["seg_per_link"][:4] = [8, 8, 10, 21]  # 33, 65, 121, 127 nodes
-    nodes = W.n_nodes(w)
-    assert nodes.max() <= 128 and (nodes > 32).sum() >= 12
-    p = M.init_params(12) * 0.5
-    net = WarmStartMLP(p)
-    cases = [(W.solver_settings(iters=10), {}),
-             (W.solver_settings(iters=5000, tol=1e-4, warm=1, beta=0.75), {}),
-             (W.solver_settings(iters=10), {"mu_side": 0.25}),
-             (W.solver_settings(iters=10, warm=2, beta=0.8, beta_net=0.5, net_rows=1, net_every=3), {})]
-    for s, extra in cases:
-        wc = dict(w)
-        for k, v in extra.items():
-            wc[k] = np.where(nodes > 32, v, 0.0)
-        runs = []
-        for pair in (share, 0.0):
-            g = Sim(wc, s)
-            for N in np.unique(nodes):
-                g.set_layout(int(N), 32, max(1, -(-int(N) // 32)))
-            g.set_pairing(pair)
-            g.set_mlp(net)
-            g.step(2)
-            runs.append(g.state_host())
-            if pair == share:
-                o = oracle.OracleSim(wc, s)
-                o.step(2, mlp=p)
-                compare(g, o, vel_floor=5e-3 if s["tol"] > 0 or s["warm"] == 2 else 0.0)
-            g.close()
-        a, b = runs
-        scale = node_scale(wc, a["pos"])
-        assert (np.linalg.norm(a["pos"] - b["pos"], axis=1) <= 1e-5 * scale).all()
-        if s["tol"] == 0:
-            assert np.array_equal(a["iters"], b["iters"])
-    net.close()
-
-
 def test_extreme_sizes_match_oracle():
     """The longest snake the lane layouts hold (128 nodes: 32 lanes x 4 nodes) beside the
     shortest (2 nodes, one stretch row), with a learned-mode-sized grid of tiny and huge
