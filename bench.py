@@ -37,16 +37,17 @@ SETTLE = 60
 TOL = 1e-4
 CAP = 5000
 SKIP = 0.5  # learned warm start: lambda0 = SKIP lambda_prev + m g h^2 network(features)
-# the learned warm start the metric is quoted on: the network on the bilateral rows
-# (stretch, yaw, pitch) at every third substep, its prediction on SKIP x the previous
-# multipliers, LEARNED_BETA x the previous multipliers at the other substeps and rows,
-# trained on targets solved from SKIP x the previous multipliers along trajectories that
-# use the network in this same configuration; PREV_BETA for the previous-multiplier start.
-# Each is the fastest value measured on the settled 16384-snake batch (network every 2nd /
-# 3rd / 4th substep: 505 k / 530 k / 498 k env-steps/s; LEARNED_BETA 0.5 ... 0.9: 458 k ...
+# the learned warm start the metric is quoted on: the network on the stretch rows at
+# every third substep, its prediction on SKIP x the previous multipliers, LEARNED_BETA x
+# the previous multipliers at the other substeps and rows, trained on targets solved from
+# SKIP x the previous multipliers along trajectories that use the network in this same
+# configuration; PREV_BETA for the previous-multiplier start.  Each is the fastest value
+# measured on the settled 16384-snake batch (network every 2nd / 3rd / 4th substep on the
+# bilateral rows: 505 k / 530 k / 498 k env-steps/s; stretch rows against bilateral rows at
+# every 3rd, each trained for its rows: 546 k / 536 k; LEARNED_BETA 0.5 ... 0.9: 458 k ...
 # 530 k (0.8) ... 517 k; PREV_BETA 0.65 ... 0.8: 409 k ... 432 k (0.75) ... 401 k); the
 # other learned variants, with the same network and weights, are reported under `modes`
-LEARNED = dict(net_rows=1, net_every=3)
+LEARNED = dict(net_rows=2, net_every=3)
 LEARNED_BETA = 0.8   # weight of lambda_prev at the learned mode's substeps without the network
 PREV_BETA = 0.75     # the previous-multiplier warm start's weight of lambda_prev
 TARGET_WARM = 1  # training targets: solves started from SKIP x the previous multipliers
