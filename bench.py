@@ -64,10 +64,10 @@ FLOP_PER_NODE_PASS = 216
 # 1,261,356-row launch of the current mlp_infer_kernel
 MLP_DRAM_BYTES_PER_ROW = (80.797440e6 + 1.975808e6) / 1261356
 # DRAM bytes per node of a split-mode launch of the 32-lane x 3-node solver kernel: ncu
-# (8.283648 MB read + 0.016640 MB written, a launch of three substeps in steady
-# locomotion, features of the bilateral rows) over the 93,177 nodes that layout owns in
-# the 4096-snake batch (the features it writes are consumed from L2 by the network)
-SPLIT_DRAM_BYTES_PER_NODE = (8.283648e6 + 0.016640e6) / 93177
+# (8.275712 MB read + 768 B written, a launch of three substeps in steady locomotion,
+# features of the stretch rows) over the 93,177 nodes that layout owns in the 4096-snake
+# batch (the features it writes are consumed from L2 by the network)
+SPLIT_DRAM_BYTES_PER_NODE = (8.275712e6 + 768.0) / 93177
 # Minimal HBM bytes of one launch per node (float4 position and velocity read + written,
 # six float multipliers read + written), per link (float2 pressures read + written) and
 # per snake (96-byte parameters, offsets, residual, update count, status).
