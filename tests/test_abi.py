@@ -90,6 +90,11 @@ def test_argument_validation_without_gpu(lib):
         cfg3 = make_config(W.solver_settings(**bad_law))
         assert lib.sim_create(ctypes.byref(cfg3), 1, prm, None, ctypes.byref(h)) == N.SIM_EINVAL, bad_law
     assert b"law" in lib.sim_last_error() or b"latency" in lib.sim_last_error()
+    for bad_net in (dict(net_rows=3), dict(net_rows=-1), dict(net_every=-1), dict(beta_net=1.5),
+                    dict(beta=1.2), dict(warm=3)):
+        cfg4 = make_config(W.solver_settings(**bad_net))
+        assert lib.sim_create(ctypes.byref(cfg4), 1, prm, None, ctypes.byref(h)) == N.SIM_EINVAL, bad_net
+        assert h.value is None
     assert lib.sim_create(ctypes.byref(cfg), 1, prm, None, None) == N.SIM_EINVAL
     # calls on a null handle
     assert lib.sim_step(None, 1) == N.SIM_EINVAL
