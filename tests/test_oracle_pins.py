@@ -545,3 +545,28 @@ def test_env_steps_are_equivariant_under_rotations_about_the_vertical(mu_side):
     va, vb = o.v[o.snake_nodes(0)], o.v[o.snake_nodes(1)]
     assert np.abs(vb - va @ Rz.T).max() < 1e-9 * np.abs(va).max()
     assert np.abs(va).max() > 1e-3  # the snakes are moving
+
+
+@pytest.mark.parametrize("mu_side,tol", [(0.0, 0.0), (0.9, 0.0), (0.0, 1e-4)])
+def test_env_steps_are_equivariant_under_horizontal_translations(mu_side, tol):
+    """The ground plane, gravity and every row depend on position differences and on
+    heights only, and the friction pair is anchored at the substep start, so two snakes
+    that differ only by a horizontal offset of their start evolve into each other
+    shifted (fixed-count passes, and to a tolerance with the same update counts); a term
+    that used an absolute horizontal position would break it."""
+    w = W.batched(n=2, seed=22, links=(3, 3))
+    for k in W.FLOAT_FIELDS:
+        w[k][1] = w[k][0]
+    off = np.array([3.75, -2.5, 0.0])
+    w["x0"][:] = [0.1, 0.1 + off[0]]
+    w["y0"][:] = [-0.2, -0.2 + off[1]]
+    w["mu_side"][:] = mu_side
+    o = oracle.OracleSim(w, W.solver_settings(iters=5000 if tol > 0 else 10, tol=tol))
+    o.step(3)
+    a, b = o.x[o.snake_nodes(0)], o.x[o.snake_nodes(1)]
+    assert np.abs(b - (a + off)).max() < 1e-9
+    va, vb = o.v[o.snake_nodes(0)], o.v[o.snake_nodes(1)]
+    assert np.abs(vb - va).max() < 1e-6 * max(1.0, np.abs(va).max())
+    assert np.abs(va).max() > 1e-3  # the snakes are moving
+    if tol > 0:
+        assert o.iters[0] == o.iters[1]
