@@ -115,6 +115,24 @@ def test_one_step_single_snake():
         assert st["resid"][0] == pytest.approx(o.resid[0], rel=1e-3)
 
 
+def test_locomotion_matches_oracle_over_5_env_steps():
+    """A twelfth of a second of locomotion (5 env-steps, the gait running, contact and
+    friction active) at a fixed 10 updates per substep, so that both sides take the same
+    passes: the GPU's FP32 state stays within the one-step bounds of the FP64 oracle's,
+    node by node, after every env-step.  (The two drift apart further on: contact and
+    friction switches amplify the rounding differences, and by the 7th env-step a
+    velocity passes the one-step bound; parity is a per-step property from common
+    states.)"""
+    w = W.batched(n=8, seed=47, links=(2, 8))
+    s = W.solver_settings(iters=10, warm=1, beta=0.75)
+    g, o = Sim(w, s), oracle.OracleSim(w, s)
+    for _ in range(5):
+        g.step(1)
+        o.step(1)
+        compare(g, o)
+    assert np.abs(o.v).max() > 1e-2  # the snakes move
+
+
 @pytest.mark.parametrize("warm", [0, 1])
 def test_one_step_ragged_batch(warm):
     w = ragged_batch()
