@@ -212,3 +212,32 @@ def test_max_over_terms_and_fixed_rows():
     x2[2, 0] += 5e-5   # node 2 moves with node 1: stretch (1, 2) exact
     # the bend rows centred on node 1 see node 2 and are still exact (straight chain)
     assert resid(w2, x2, x2) == pytest.approx(0.0, abs=1e-12)
+
+
+@pytest.mark.parametrize("mu_side", [0.0, 0.3])
+def test_residual_is_invariant_under_rotations_about_z_and_horizontal_shifts(mu_side):
+    """Random states of a 7-node snake (positions near the ground, substep-start
+    positions, pressures, multipliers of every kind): rotating the whole state about the
+    vertical (positions, start positions and the friction pair in world x / y) and
+    shifting it horizontally leaves the residual unchanged, since every term is a
+    length measured in the row's own frame or along z."""
+    rng = np.random.default_rng(7)
+    w = snake(mu_side=mu_side)
+    w["seg_per_link"][:] = 6
+    L0, r = float(w["L0"][0]), float(w["radius"][0])
+    for _ in range(20):
+        x = np.array([[i * L0, 0.0, r] for i in range(7)]) + rng.normal(0, 0.3 * L0, (7, 3))
+        xs = x + rng.normal(0, 0.05 * L0, (7, 3))
+        press = rng.uniform(0, 1, (1, 2))
+        lam = rng.normal(0, 1e-6, (7, 6))
+        lam[:, 3] = np.abs(lam[:, 3])
+        ref = resid(w, x, xs, press, lam)
+        th = rng.uniform(0, 2 * math.pi)
+        c, s_ = math.cos(th), math.sin(th)
+        R = np.array([[c, -s_, 0.0], [s_, c, 0.0], [0.0, 0.0, 1.0]])
+        off = np.array([rng.uniform(-3, 3), rng.uniform(-3, 3), 0.0])
+        lr = lam.copy()
+        lr[:, 4] = c * lam[:, 4] - s_ * lam[:, 5]
+        lr[:, 5] = s_ * lam[:, 4] + c * lam[:, 5]
+        got = resid(w, x @ R.T + off, xs @ R.T + off, press, lr)
+        assert ref > 0 and got == pytest.approx(ref, rel=1e-9)
