@@ -426,6 +426,12 @@ def run_gpu(args):
                          "kernel": "snake_solver_kernel<%d, %d, 1, 0> (learned mode, %d lanes x %d nodes "
                                    "per lane)" % (dom[1], dom[0], dom[0], dom[1]),
                          "ms_per_launch": dom_ms / dom_n,
+                         "timing": "the layouts' launches one after another, an event pair around each; "
+                                   "with the batch in steady locomotion a launch lasts as long as its "
+                                   "slowest snake (6-13x its class's mean updates per env-step), so this "
+                                   "fraction counts the SMs waiting for it; `solver_family` is the same "
+                                   "kernels overlapped in the timed step, `fixed_iterations` the pass "
+                                   "without slow snakes",
                          "flop_per_node_pass": FLOP_PER_NODE_PASS,
                          "solver_family": {"achieved": family, "frac": family / alu_peak,
                                            "note": "all layout kernels of the learned step, step time "
